@@ -1,0 +1,352 @@
+"""Benchmark of the wedge-sampling hot path on GB300.
+
+One step = the whole path on one synthetic graph: edge list (resident in HBM)
+-> CSR with degrees (expand, radix sort, dedup, offset scan) -> degree bins
+and wedge prefix -> per-bin and global wedge sampling with closure checks and
+tallies -> FP64 estimates. Workload: Graph500 Kronecker (R-MAT 0.57/0.19/0.19/
+0.05), scale 28, edge factor 16 (4,294,967,296 generated edges, ids permuted),
+bins 2^i <= d < 2^(i+1), 950,114 samples per nonempty bin and globally
+(eps = 0.002, delta = 0.001), Philox seed 7.
+
+Prints one JSON line. `value` is seconds per million undirected edges of the
+whole step (lower is better); `gwedges_checked_per_s` is the sampling stage
+alone. `e2e` runs the same step through the C ABI from pinned host buffers,
+host-to-device copies inside the timed region. `--impl reference` times the
+CPU oracle on the host cores on a bounded sample of the workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gwedges checked/s and s per M edges at Kronecker scale 28; batched vs plain"
+K_SAMPLES = 950114  # eps = 0.002, delta = 0.001 (Thm 3.1 bound 950,113 rounded as quoted)
+SEED = 7
+TAU, OMEGA = 1, 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=28)
+    ap.add_argument("--edgefactor", type=int, default=16)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# --------------------------------------------------------------------------
+# Clock sampling during the timed region
+# --------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# Reference arm: the CPU oracle on the host cores
+# --------------------------------------------------------------------------
+
+def oracle_step(scale: int, edgefactor: int, k: int):
+    """One full oracle pass (CSR, bins, sampling, estimates) on a Kronecker
+    graph of the given scale; returns (seconds, undirected edges, samples)."""
+    import graphgen
+    import oracle
+    from oracle.estimate import estimate
+    src, dst = graphgen.kronecker_host(scale, n_edges=edgefactor << scale, seed=1)
+    t0 = time.perf_counter()
+    off, adj = oracle.csr(src, dst, 1 << scale)
+    bb = oracle.bins(off, TAU, OMEGA)
+    r = oracle.sample(off, adj, TAU, OMEGA, SEED, k, k)
+    estimate(bb["p_b"], r["counts"], r["glob"], 0.001)
+    dt = time.perf_counter() - t0
+    n_samples = int(r["counts"][:, 0].sum()) + int(r["glob"][0])
+    return dt, adj.shape[0] // 2, n_samples
+
+
+def cpu_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # Bounded sample: the largest scale whose whole run fits a few minutes.
+    scale = 20 if args.steps + args.warmup <= 8 else 18
+    for _ in range(args.warmup):
+        oracle_step(scale, args.edgefactor, K_SAMPLES)
+    times, m, ns = [], 0, 0
+    for _ in range(args.steps):
+        dt, m, ns = oracle_step(scale, args.edgefactor, K_SAMPLES)
+        times.append(dt)
+    t = sum(times) / len(times)
+    value = t / (m / 1e6)
+    sample = (f"Kronecker scale {scale} (edge factor {args.edgefactor}), full oracle pass: CSR, bins, "
+              f"{K_SAMPLES} samples per nonempty bin and globally, estimates")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/Medge", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"kronecker-s{scale}-ef{args.edgefactor} (bounded sample of kronecker-s28)",
+                       "scale": scale, "k_per_bin": K_SAMPLES, "k_global": K_SAMPLES, "tau": TAU, "omega": OMEGA},
+            "gwedges_checked_per_s": ns / t / 1e9,
+            "cpu_baseline": {"value": value, "unit": "s/Medge", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "s/Medge", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# Our arm
+# --------------------------------------------------------------------------
+
+ALG_BYTES = {
+    # algorithmic DRAM bytes per launch, from the sizes of one step
+    "sort_onesweep_pass": lambda z: 16 * z["nkeys"],
+    "sort_histogram": lambda z: 8 * z["nkeys"],
+    "expand_edges": lambda z: 24 * z["n_edges"],
+    "dedup_rows": lambda z: 8 * z["nkeys"] + 4 * z["n_adj"] + 4 * z["n"],
+    "scan_degrees": lambda z: 12 * z["n"],
+    "bin_count": lambda z: 4 * z["n"],
+    "bin_scatter": lambda z: 4 * z["n"] + 12 * z["n2"],
+}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import graphgen
+    import paper_1301_5887_gb300 as wedge
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    __graft_entry__.build() if rank == 0 and world == 1 else None
+    if world > 1:
+        if rank == 0:
+            __graft_entry__.build()
+        dist.barrier()
+    wedge.load()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+
+    scale, ef = args.scale, args.edgefactor
+    n = 1 << scale
+    n_edges = ef << scale
+    src = torch.empty(n_edges, dtype=torch.int32, device="cuda")
+    dst = torch.empty(n_edges, dtype=torch.int32, device="cuda")
+    graphgen.kronecker_device(scale, src.data_ptr(), dst.data_ptr(), n_edges, stream.cuda_stream, seed=1)
+    torch.cuda.synchronize()
+
+    info = {}
+
+    def step(s_in, d_in):
+        g = wedge.graph_build(s_in, d_in, n)
+        b = wedge.bin(g, tau=TAU, omega=OMEGA)
+        c = wedge.sample(g, b, seed=SEED, k_per_bin=K_SAMPLES, k_global=K_SAMPLES)
+        est = wedge.estimate(c, 0.001)
+        gi, bi = g.info(), b.info()
+        info.update(n_adj=gi.n_adj, n2=bi.n_wedge_vertices, n_bins=bi.n_bins,
+                    samples=int(c.k_b.sum()) + c.k_global, c_hat=est["c_hat"], c_hat_global=est["c_hat_global"],
+                    n_streams=int((c.k_b > 0).sum()) + (1 if c.k_global else 0))
+        b.free()
+        g.free()
+
+    for _ in range(args.warmup):
+        step(src, dst)
+
+    # Timed region: device-resident inputs (34 GB at scale 28 >> 129 MB L2).
+    clocks = Clocks(dev)
+    clocks.start()
+    wedge.profile_reset()
+    wedge.profile_enable(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(src, dst)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wedge.profile_enable(False)
+    ms_total = e0.elapsed_time(e1)
+    prof = wedge.profile_read()
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    m = info["n_adj"] // 2
+    value = (ms_step / 1e3) / (world * m / 1e6)
+    samp = prof.get("sample_closure", {"total_ms": 0.0, "launches": 0})
+    samp_ms = samp["total_ms"] / max(samp["launches"], 1)
+    gwps = world * info["samples"] / (samp_ms / 1e3) / 1e9 if samp_ms > 0 else None
+    launches = sum(v["launches"] for v in prof.values())
+
+    sizes = {"nkeys": 2 * n_edges, "n_edges": n_edges, "n_adj": info["n_adj"], "n": n, "n2": info["n2"]}
+    top = max((k for k in prof if k in ALG_BYTES), key=lambda k: prof[k]["total_ms"])
+    peaks, peak_kind = measured_peaks()
+    avg_ms = prof[top]["total_ms"] / prof[top]["launches"]
+    achieved = ALG_BYTES[top](sizes) / (avg_ms / 1e3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            tr = json.load(f)
+        ent = tr.get(top)
+        if ent and ent.get("scale") and ent.get("bytes_per_launch"):
+            traffic = ent["bytes_per_launch"] * (sizes["nkeys"] / ent["nkeys"]) if "nkeys" in ent else None
+    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "alg_bytes_per_launch": ALG_BYTES[top](sizes), "avg_launch_ms": avg_ms}
+
+    kernels = {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["total_ms"] / args.steps,
+                   "share": v["total_ms"] / max(ms_total, 1e-9)} for k, v in prof.items()}
+
+    # e2e: the same step from pinned host buffers through the C ABI.
+    e2e = None
+    if args.e2e_steps > 0:
+        hsrc = torch.empty(n_edges, dtype=torch.int32, pin_memory=True)
+        hdst = torch.empty(n_edges, dtype=torch.int32, pin_memory=True)
+        hsrc.copy_(src)
+        hdst.copy_(dst)
+        del src, dst
+        torch.cuda.synchronize()
+        step(hsrc, hdst)  # warm the staging path
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            step(hsrc, hdst)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        if world > 1:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        d2h = 8 + 16 + 2 * 8 * info["n_bins"] + 4 + 8 * (4 * info["n_streams"] + 34 * 34)
+        e2e = {"value": dt / (world * m / 1e6), "unit": "s/Medge", "h2d_bytes_per_step": 8 * n_edges,
+               "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
+        del hsrc, hdst
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, mm, ns = oracle_step(20, ef, K_SAMPLES)
+        cpu = {"value": dt / (mm / 1e6), "unit": "s/Medge", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"Kronecker scale 20 (edge factor {ef}, {mm} undirected edges), full oracle pass with "
+                         f"{K_SAMPLES} samples per nonempty bin and globally; same metric",
+               "seconds": dt, "gwedges_checked_per_s": ns / dt / 1e9}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "s/Medge", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": f"kronecker-s{scale}-ef{ef}", "scale": scale, "edgefactor": ef,
+                           "n_vertices": n, "generated_edges": n_edges, "undirected_edges": m, "tau": TAU,
+                           "omega": OMEGA, "k_per_bin": K_SAMPLES, "k_global": K_SAMPLES, "seed": SEED,
+                           "bins": info["n_bins"], "samples_per_step": info["samples"],
+                           "l2": f"inputs {8 * n_edges / 1e9:.1f} GB > 129 MB L2, no flush needed",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "gwedges_checked_per_s": gwps, "sampling_ms": samp_ms,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
+                "clocks": clk, "kernels": kernels,
+                "estimates": {"c_hat": info["c_hat"], "c_hat_global": info["c_hat_global"]}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

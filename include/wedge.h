@@ -1,0 +1,271 @@
+/*
+ * wedge.h — C ABI of the GB300 wedge-sampling library.
+ *
+ * Degree-binned wedge sampling for clustering coefficients and triangle
+ * counts, after Kolda, Pinar, Plantenga, Seshadhri and Task, "Counting
+ * Triangles in Massive Graphs with MapReduce" (SIAM J. Sci. Comput., 2014).
+ * The paper states the problem (Sec. 2, Sec. 4.1): from an undirected edge
+ * list, compute per-bin and global clustering coefficients and triangle
+ * counts by sampling wedges uniformly (Sec. 3) and checking their closure.
+ * Every step below runs in this library's CUDA kernels for sm_103a.
+ *
+ * Conventions for every call:
+ *   - Streams: all device work is ordered on the caller's stream `s` (a
+ *     cudaStream_t; NULL means the legacy default stream). Calls that return
+ *     host results synchronise that stream before returning.
+ *   - Pointers: "device" arguments are CUDA device pointers; "host or device"
+ *     arguments may be either (the library asks the CUDA driver which).
+ *   - Ownership: the caller owns every buffer it passes and may reuse it once
+ *     the call returns; the library never retains caller pointers. The library
+ *     owns the opaque handles it returns; free them with the matching *_free.
+ *   - Errors: every call returns a wedge_status. On error no handle is
+ *     produced, nothing leaks, and wedge_last_error() describes the failure
+ *     (a per-thread string valid until the next call on that thread).
+ *   - Memory: device memory comes from a library-owned stream-ordered pool
+ *     (cudaMallocAsync) on the current device; wedge_trim() releases the
+ *     pool's cached memory.
+ */
+#ifndef WEDGE_H
+#define WEDGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define WEDGE_API __attribute__((visibility("default")))
+#else
+#define WEDGE_API
+#endif
+
+typedef struct CUstream_st* wedge_stream; /* cudaStream_t */
+
+typedef enum {
+  WEDGE_OK = 0,
+  WEDGE_EINVAL = 1,    /* bad argument (see each call) */
+  WEDGE_ENOMEM = 2,    /* device or host allocation failed */
+  WEDGE_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+  WEDGE_ETIMEOUT = 4,  /* a bounded device-side wait gave up (no fault, context intact) */
+  WEDGE_EOVERFLOW = 5  /* a count does not fit its type (degree >= 2^31, wedges >= 2^64) */
+} wedge_status;
+
+/* Largest number of bins (bin ids 0 .. WEDGE_MAX_BINS-1; id 0 is never used). */
+#define WEDGE_MAX_BINS 256
+/* Bins of the closed-wedge statistics histogram: BinId with tau=2, omega=2 (Sec. 5.7). */
+#define WEDGE_STAT_BINS 34
+
+typedef struct wedge_graph wedge_graph; /* device CSR of an undirected simple graph */
+typedef struct wedge_bins wedge_bins;   /* degree bins, ordered vertex list and wedge prefix */
+
+WEDGE_API const char* wedge_status_str(wedge_status st);
+WEDGE_API const char* wedge_last_error(void);
+/* Library version, e.g. 0x000100 for 0.1.0. */
+WEDGE_API uint32_t wedge_version(void);
+/* sizeof of the ABI structs, for bindings to check their layouts: fills up to
+ * cap of [graph_info, bins_info, sample_params, record, counts, estimates,
+ * kernel_stat] and returns 7. */
+WEDGE_API int wedge_abi_sizes(uint64_t* sizes, int cap);
+
+/* --------------------------------------------------------------------------
+ * Graph: edge list -> CSR with degrees.
+ *
+ * Input (Sec. 4.1, Sec. 5.1): n_edges pairs (src[e], dst[e]) of vertex ids
+ * in [0, n_vertices). The graph is undirected: {u,v} is an edge iff u != v and
+ * (u,v) or (v,u) appears; repeated pairs collapse and self-loops are dropped.
+ * src and dst are host or device int32 arrays of n_edges entries, read before
+ * the call returns. Output: *out, a graph whose adjacency rows are sorted
+ * ascending (degree d_v = row length, Alg. Phase 1a).
+ * Errors: EINVAL if n_edges < 0, n_vertices < 1, n_vertices > 2^31 - 1, a
+ * pointer is NULL while n_edges > 0, or an id is outside [0, n_vertices);
+ * ENOMEM; ECUDA; ETIMEOUT (a scan or sort look-back wait gave up).
+ * ------------------------------------------------------------------------ */
+WEDGE_API wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst, int64_t n_edges, int32_t n_vertices,
+                               wedge_stream s, wedge_graph** out);
+WEDGE_API void wedge_graph_free(wedge_graph* g);
+
+typedef struct {
+  int32_t n_vertices;
+  int32_t id_bits;      /* smallest b >= 1 with 2^b >= n_vertices */
+  int64_t n_adj;        /* 2m: adjacency entries (m undirected edges) */
+  int64_t n_input_edges;/* n_edges given to wedge_graph_build */
+  int32_t max_degree;
+  const int64_t* off;   /* device, n_vertices + 1 row offsets (borrowed; valid until wedge_graph_free) */
+  const int32_t* adj;   /* device, n_adj neighbour ids, each row ascending */
+  const int32_t* deg;   /* device, n_vertices degrees */
+} wedge_graph_info;
+WEDGE_API wedge_status wedge_graph_get_info(const wedge_graph* g, wedge_graph_info* out);
+
+/* Copy the CSR into caller buffers (host or device; any may be NULL to skip):
+ * off[n_vertices + 1], adj[n_adj], deg[n_vertices]. Synchronises s. */
+WEDGE_API wedge_status wedge_graph_copy(const wedge_graph* g, int64_t* off, int32_t* adj, int32_t* deg, wedge_stream s);
+
+/* --------------------------------------------------------------------------
+ * Bins: degree bins (Sec. 4.2) and per-bin wedge totals (Alg. Phase 1b).
+ *
+ * tau singleton bins {1}..{tau}, then bins growing by the integer factor
+ * omega: BinLoDeg(k) = k for k <= tau, else (omega^(k-tau) - 1)/(omega - 1) + tau
+ * (Eq. BinLoDeg); BinId(d) = the k with BinLoDeg(k) <= d < BinLoDeg(k+1)
+ * (Eq. BinId, evaluated exactly). tau = 1, omega = 2 gives 2^i <= d < 2^(i+1);
+ * tau = 2, omega = 2 is the paper's default; tau = 1 with a huge omega is one
+ * bin of all degrees >= 2.
+ * Output: n_b, p_b = sum of C(d,2) per bin; the vertices with d >= 2 ordered
+ * by (bin, id) as L; and the wedge prefix W[j] = sum of C(d,2) over L[0..j).
+ * Errors: EINVAL if tau < 1, omega < 2, omega >= 2^32, or the graph's largest
+ * degree falls in a bin id >= WEDGE_MAX_BINS (use a smaller tau or larger
+ * omega); EOVERFLOW if the total wedge count does not fit in uint64.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  uint32_t tau;
+  uint64_t omega;
+} wedge_bin_params;
+
+WEDGE_API wedge_status wedge_bin(const wedge_graph* g, const wedge_bin_params* bp, wedge_stream s, wedge_bins** out);
+WEDGE_API void wedge_bins_free(wedge_bins* b);
+
+typedef struct {
+  uint32_t n_bins;                       /* bin ids 1 .. n_bins-1 are populated up to the max degree */
+  uint32_t tau;
+  uint64_t omega;
+  uint64_t lo_deg[WEDGE_MAX_BINS];       /* BinLoDeg(k) */
+  uint64_t hi_deg[WEDGE_MAX_BINS];       /* BinLoDeg(k+1) - 1 */
+  uint64_t n_b[WEDGE_MAX_BINS];          /* vertices per bin (degree >= 1) */
+  uint64_t p_b[WEDGE_MAX_BINS];          /* wedges centred in the bin */
+  int64_t start[WEDGE_MAX_BINS + 1];     /* bin k's vertices are L[start[k] .. start[k+1]) */
+  uint64_t p_total;                      /* p = sum_k p_b */
+  int64_t n_wedge_vertices;              /* vertices with d >= 2 (length of L) */
+  const int32_t* L;                      /* device, n_wedge_vertices ids, ordered by (bin, id) */
+  const uint64_t* W;                     /* device, n_wedge_vertices + 1 prefix sums */
+} wedge_bins_info;
+WEDGE_API wedge_status wedge_bins_get_info(const wedge_bins* b, wedge_bins_info* out);
+
+/* Copy L[n_wedge_vertices] and W[n_wedge_vertices + 1] into caller buffers
+ * (host or device; either may be NULL to skip). Synchronises s. */
+WEDGE_API wedge_status wedge_bins_copy(const wedge_bins* b, int32_t* L, uint64_t* W, wedge_stream s);
+
+/* --------------------------------------------------------------------------
+ * Sampling: uniform wedges per bin and globally, closure check, tally.
+ *
+ * For every bin k with p_b > 0: k_per_bin i.i.d. wedges of W_k, each chosen
+ * by picking the centre with probability C(d,2)/p_b and then two distinct
+ * neighbours (Sec. 3.2; Thm 3.2, Thm 3.3). Each wedge is closed iff its
+ * endpoints are adjacent (Alg. Phase 3b) and is tallied (Alg. Phase 4c) as
+ * q0 (open) or q_{1 + [BinId(d1)=k] + [BinId(d2)=k]} (closed).
+ * The global stream draws k_global wedges uniformly from all of W (one bin of
+ * every degree >= 2, Sec. 4.2) and counts the closed ones; its closed wedges
+ * are uniform triangles (Thm 3.4) and feed the statistics histogram
+ * stats[BinId22(d_min)][BinId22(d_max)] (tau = 2, omega = 2, Sec. 5.7).
+ *
+ * Random words: Philox4x32-10 (Salmon et al., SC 2011), one call per sample,
+ * counter (s mod 2^32, s div 2^32, k, tag) with tag 0 per-bin (k = bin id) and
+ * tag 1 global (k = 0), key (seed mod 2^32, seed div 2^32). Words r0..r3 map
+ * to a sample as: t = floor((r0 + 2^32 r1) p_b / 2^64), centre = L[j] with
+ * W[j] - W[start] <= t < W[j+1] - W[start]; u = floor((r2 + 2^32 r3) d(d-1) / 2^64),
+ * i = u div (d-1), j' = u mod (d-1), j = j' + [j' >= i], endpoints = the i-th
+ * and j-th entries of the centre's ascending adjacency row. Results therefore
+ * depend only on (graph, bins, seed, budgets), never on launch shape.
+ *
+ * Budgets: k_per_bin (k_global) = 0 means ceil(0.5 eps^-2 ln(2/delta)) (Thm 3.1).
+ * records: optional device buffer of k_global wedge_record entries, written
+ * for the global stream in sample order (NULL: none).
+ * Errors: EINVAL if eps or delta is outside (0,1) while a budget is 0,
+ * bins do not belong to g, or records is set with WEDGE_FLAG_NO_GLOBAL;
+ * ECUDA; ENOMEM.
+ * ------------------------------------------------------------------------ */
+#define WEDGE_FLAG_NO_GLOBAL 0x1u  /* skip the global stream */
+#define WEDGE_FLAG_NO_BINS 0x2u    /* skip the per-bin streams */
+
+typedef struct {
+  uint64_t seed;
+  double eps;
+  double delta;
+  uint64_t k_per_bin;
+  uint64_t k_global;
+  uint32_t flags;
+  void* records; /* device wedge_record[k_global] or NULL */
+} wedge_sample_params;
+
+typedef struct {
+  int32_t v0, v1, v2; /* centre, endpoints */
+  int32_t closed;     /* 1 if {v1, v2} is an edge */
+  int32_t d0, d1, d2; /* degrees */
+  int32_t reserved;
+} wedge_record;
+
+typedef struct {
+  uint32_t n_bins;
+  uint64_t k_b[WEDGE_MAX_BINS];          /* samples drawn per bin */
+  uint64_t q[WEDGE_MAX_BINS][4];         /* Alg. Phase 4c tallies q0..q3 */
+  uint64_t n_b[WEDGE_MAX_BINS];          /* copied from the bins */
+  uint64_t p_b[WEDGE_MAX_BINS];
+  uint64_t p_total;
+  uint64_t k_global;
+  uint64_t closed_global;
+  uint64_t stats[WEDGE_STAT_BINS][WEDGE_STAT_BINS];
+} wedge_counts;
+
+/* Host `out` is filled after the stream is synchronised. */
+WEDGE_API wedge_status wedge_sample(const wedge_graph* g, const wedge_bins* b, const wedge_sample_params* sp, wedge_stream s,
+                          wedge_counts* out);
+
+/* Smallest k with k >= 0.5 eps^-2 ln(2/delta) (Thm 3.1); 0 if eps or delta is outside (0,1). */
+WEDGE_API uint64_t wedge_hoeffding_k(double eps, double delta);
+
+/* --------------------------------------------------------------------------
+ * Estimates (pure host, FP64).
+ *   c_b = (q1+q2+q3)/k_b (Thm 3.2), t_b = p_b (q1 + q2/2 + q3/3)/k_b (Thm 3.3),
+ *   eps_b = sqrt(ln(2/delta) / (2 k_b)) (Thm 3.1 solved for eps);
+ *   c_hat = sum_b (p_b/p) c_b, t_hat = c_hat p/3 (Eq. global_est);
+ *   global stream: c_hat_global = closed/k_global, t_hat_global = c_hat_global p/3.
+ * Bins with k_b = 0 report zeros. Errors: EINVAL for NULL or delta outside (0,1).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  uint32_t n_bins;
+  double c_b[WEDGE_MAX_BINS];
+  double t_b[WEDGE_MAX_BINS];
+  double eps_b[WEDGE_MAX_BINS];
+  double p_total;
+  double c_hat;
+  double t_hat;
+  double c_hat_global;
+  double t_hat_global;
+  double eps_global;
+} wedge_estimates;
+
+WEDGE_API wedge_status wedge_estimate(const wedge_counts* c, double delta, wedge_estimates* out);
+
+/* --------------------------------------------------------------------------
+ * Closure and class of given wedges (Alg. Phase 3b, Alg. Phase 4c) through the
+ * same device code the sampler uses, without randomness: q[i] = 0 if
+ * {v1[i], v2[i]} is not an edge, else 1 + [BinId(d(v1))=k] + [BinId(d(v2))=k]
+ * with k = BinId(d(v0[i])). v0, v1, v2, q: device arrays of n_wedges entries.
+ * Errors: EINVAL if n_wedges < 0 or an id is outside [0, n) (q is 255 there).
+ * ------------------------------------------------------------------------ */
+WEDGE_API wedge_status wedge_classify(const wedge_graph* g, const wedge_bins* b, int64_t n_wedges, const int32_t* v0,
+                            const int32_t* v1, const int32_t* v2, uint8_t* q, wedge_stream s);
+
+/* --------------------------------------------------------------------------
+ * Tracing: per-kernel device time from CUDA events recorded on the launching
+ * stream around each launch (when enabled), and launch counts (always).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  char name[48];
+  uint64_t launches;
+  double total_ms; /* 0 unless timing was enabled */
+} wedge_kernel_stat;
+
+WEDGE_API void wedge_profile_enable(int enable_timing);
+WEDGE_API void wedge_profile_reset(void);
+/* Fills up to cap entries; returns the number of kernels recorded. Synchronises pending events. */
+WEDGE_API int wedge_profile_read(wedge_kernel_stat* out, int cap);
+
+/* Release cached device memory of the library's pool on the current device. */
+WEDGE_API wedge_status wedge_trim(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WEDGE_H */

@@ -1,0 +1,371 @@
+"""Python binding of libwedge.so, the GB300 wedge-sampling library.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels behind the C ABI declared in include/wedge.h. The functions keep
+the C names without the ``wedge_`` prefix:
+
+    graph_build(src, dst, n_vertices, stream) -> Graph      (wedge_graph_build)
+    bin(graph, tau, omega, stream) -> Bins                  (wedge_bin)
+    sample(graph, bins, seed, eps, delta, k_per_bin, k_global, ...) -> Counts
+    estimate(counts, delta) -> dict                         (wedge_estimate)
+    classify(graph, bins, v0, v1, v2, q, stream)            (wedge_classify)
+    hoeffding_k(eps, delta)
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; host arrays are
+copied to the device inside the library. PyTorch supplies device memory and
+streams only. If libwedge.so is missing the import of the library fails
+loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_PKG, "libwedge.so")
+
+MAX_BINS = 256
+STAT_BINS = 34
+FLAG_NO_GLOBAL = 0x1
+FLAG_NO_BINS = 0x2
+
+STATUS = {0: "WEDGE_OK", 1: "WEDGE_EINVAL", 2: "WEDGE_ENOMEM", 3: "WEDGE_ECUDA", 4: "WEDGE_ETIMEOUT",
+          5: "WEDGE_EOVERFLOW"}
+
+
+class WedgeError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+# ---------------------------------------------------------------------------
+# ABI structs (mirror include/wedge.h)
+# ---------------------------------------------------------------------------
+_vp = ctypes.c_void_p
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int32), ("id_bits", ctypes.c_int32), ("n_adj", ctypes.c_int64),
+                ("n_input_edges", ctypes.c_int64), ("max_degree", ctypes.c_int32), ("off", _vp), ("adj", _vp),
+                ("deg", _vp)]
+
+
+class BinParams(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_uint32), ("omega", ctypes.c_uint64)]
+
+
+class BinsInfo(ctypes.Structure):
+    _fields_ = [("n_bins", ctypes.c_uint32), ("tau", ctypes.c_uint32), ("omega", ctypes.c_uint64),
+                ("lo_deg", ctypes.c_uint64 * MAX_BINS), ("hi_deg", ctypes.c_uint64 * MAX_BINS),
+                ("n_b", ctypes.c_uint64 * MAX_BINS), ("p_b", ctypes.c_uint64 * MAX_BINS),
+                ("start", ctypes.c_int64 * (MAX_BINS + 1)), ("p_total", ctypes.c_uint64),
+                ("n_wedge_vertices", ctypes.c_int64), ("L", _vp), ("W", _vp)]
+
+
+class SampleParams(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("eps", ctypes.c_double), ("delta", ctypes.c_double),
+                ("k_per_bin", ctypes.c_uint64), ("k_global", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("records", _vp)]
+
+
+class Record(ctypes.Structure):
+    _fields_ = [(x, ctypes.c_int32) for x in ("v0", "v1", "v2", "closed", "d0", "d1", "d2", "reserved")]
+
+
+class CountsStruct(ctypes.Structure):
+    _fields_ = [("n_bins", ctypes.c_uint32), ("k_b", ctypes.c_uint64 * MAX_BINS),
+                ("q", (ctypes.c_uint64 * 4) * MAX_BINS), ("n_b", ctypes.c_uint64 * MAX_BINS),
+                ("p_b", ctypes.c_uint64 * MAX_BINS), ("p_total", ctypes.c_uint64), ("k_global", ctypes.c_uint64),
+                ("closed_global", ctypes.c_uint64), ("stats", (ctypes.c_uint64 * STAT_BINS) * STAT_BINS)]
+
+
+class EstimatesStruct(ctypes.Structure):
+    _fields_ = [("n_bins", ctypes.c_uint32), ("c_b", ctypes.c_double * MAX_BINS), ("t_b", ctypes.c_double * MAX_BINS),
+                ("eps_b", ctypes.c_double * MAX_BINS), ("p_total", ctypes.c_double), ("c_hat", ctypes.c_double),
+                ("t_hat", ctypes.c_double), ("c_hat_global", ctypes.c_double), ("t_hat_global", ctypes.c_double),
+                ("eps_global", ctypes.c_double)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
+_STRUCTS = [GraphInfo, BinsInfo, SampleParams, Record, CountsStruct, EstimatesStruct, KernelStat]
+
+# Every symbol include/wedge.h declares.
+EXPORTS = ["wedge_status_str", "wedge_last_error", "wedge_version", "wedge_abi_sizes", "wedge_graph_build",
+           "wedge_graph_free", "wedge_graph_get_info", "wedge_graph_copy", "wedge_bin", "wedge_bins_free",
+           "wedge_bins_get_info", "wedge_bins_copy", "wedge_sample", "wedge_hoeffding_k", "wedge_estimate", "wedge_classify",
+           "wedge_profile_enable", "wedge_profile_reset", "wedge_profile_read", "wedge_trim"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _SO
+
+
+def load():
+    """Load libwedge.so (built by build.py / __graft_entry__.build()). Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_SO):
+        raise ImportError(f"libwedge.so is not built ({_SO}); run __graft_entry__.build() — there is no CPU fallback")
+    lib = ctypes.CDLL(_SO)
+    i32, i64, u32, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+    P = ctypes.c_void_p
+    st = ctypes.c_int
+    sig = {
+        "wedge_status_str": ([st], ctypes.c_char_p),
+        "wedge_last_error": ([], ctypes.c_char_p),
+        "wedge_version": ([], u32),
+        "wedge_abi_sizes": ([P, ctypes.c_int], ctypes.c_int),
+        "wedge_graph_build": ([P, P, i64, i32, P, P], st),
+        "wedge_graph_free": ([P], None),
+        "wedge_graph_get_info": ([P, P], st),
+        "wedge_graph_copy": ([P, P, P, P, P], st),
+        "wedge_bin": ([P, P, P, P], st),
+        "wedge_bins_free": ([P], None),
+        "wedge_bins_get_info": ([P, P], st),
+        "wedge_bins_copy": ([P, P, P, P], st),
+        "wedge_sample": ([P, P, P, P, P], st),
+        "wedge_hoeffding_k": ([dbl, dbl], u64),
+        "wedge_estimate": ([P, dbl, P], st),
+        "wedge_classify": ([P, P, i64, P, P, P, P, P], st),
+        "wedge_profile_enable": ([ctypes.c_int], None),
+        "wedge_profile_reset": ([], None),
+        "wedge_profile_read": ([P, ctypes.c_int], ctypes.c_int),
+        "wedge_trim": ([], st),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    sizes = (ctypes.c_uint64 * 8)()
+    lib.wedge_abi_sizes(sizes, 8)
+    for i, S in enumerate(_STRUCTS):
+        if sizes[i] != ctypes.sizeof(S):
+            raise ImportError(f"ABI mismatch for {S.__name__}: C {sizes[i]} bytes, binding {ctypes.sizeof(S)}")
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise WedgeError(status, _lib.wedge_last_error().decode())
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _ptr(a, dtype=None):
+    """(pointer, keepalive) of a contiguous torch tensor or numpy array."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if dtype is not None:
+                want = {np.int32: torch.int32, np.uint8: torch.uint8, np.int64: torch.int64}[dtype]
+                if a.dtype != want:
+                    raise TypeError(f"expected {want}, got {a.dtype}")
+            a = a.contiguous()
+            return a.data_ptr(), a
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype) if dtype is not None else np.ascontiguousarray(a)
+    return arr.ctypes.data, arr
+
+
+# ---------------------------------------------------------------------------
+# Handles
+# ---------------------------------------------------------------------------
+
+class Graph:
+    """Owns a wedge_graph handle (device CSR)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> GraphInfo:
+        gi = GraphInfo()
+        _check(load().wedge_graph_get_info(self._h, ctypes.byref(gi)))
+        return gi
+
+    def copy(self, off=None, adj=None, deg=None, stream=None):
+        """Copy the CSR into caller arrays (host or device)."""
+        po = _ptr(off, np.int64)[0] if off is not None else 0
+        pa = _ptr(adj, np.int32)[0] if adj is not None else 0
+        pd = _ptr(deg, np.int32)[0] if deg is not None else 0
+        _check(load().wedge_graph_copy(self._h, po, pa, pd, _stream_handle(stream)))
+
+    def csr_numpy(self):
+        gi = self.info()
+        off = np.empty(gi.n_vertices + 1, np.int64)
+        adj = np.empty(max(gi.n_adj, 1), np.int32)
+        deg = np.empty(gi.n_vertices, np.int32)
+        self.copy(off, adj, deg)
+        return off, adj[: gi.n_adj], deg
+
+    def free(self):
+        if self._h:
+            load().wedge_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Bins:
+    """Owns a wedge_bins handle (bin table, L and W on the device)."""
+
+    def __init__(self, handle, graph: Graph):
+        self._h = handle
+        self.graph = graph
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> BinsInfo:
+        bi = BinsInfo()
+        _check(load().wedge_bins_get_info(self._h, ctypes.byref(bi)))
+        return bi
+
+    def copy(self, L=None, W=None, stream=None):
+        """Copy L (int32) and W (uint64, passed as an int64 or uint64 array) into caller arrays."""
+        pl = _ptr(L, np.int32)[0] if L is not None else 0
+        pw = _ptr(W)[0] if W is not None else 0
+        _check(load().wedge_bins_copy(self._h, pl, pw, _stream_handle(stream)))
+
+    def arrays_numpy(self):
+        bi = self.info()
+        L = np.empty(max(bi.n_wedge_vertices, 1), np.int32)
+        W = np.empty(bi.n_wedge_vertices + 1, np.uint64)
+        self.copy(L, W)
+        return L[: bi.n_wedge_vertices], W
+
+    def free(self):
+        if self._h:
+            load().wedge_bins_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def graph_build(src, dst, n_vertices: int, stream=None) -> Graph:
+    lib = load()
+    ps, ks = _ptr(src, np.int32)
+    pd, kd = _ptr(dst, np.int32)
+    n_edges = int(ks.shape[0]) if hasattr(ks, "shape") else len(ks)
+    h = ctypes.c_void_p()
+    _check(lib.wedge_graph_build(ps, pd, n_edges, int(n_vertices), _stream_handle(stream), ctypes.byref(h)))
+    return Graph(h.value)
+
+
+def bin(graph: Graph, tau: int = 1, omega: int = 2, stream=None) -> Bins:  # noqa: A001 - C name
+    lib = load()
+    bp = BinParams(tau, omega)
+    h = ctypes.c_void_p()
+    _check(lib.wedge_bin(graph.handle, ctypes.byref(bp), _stream_handle(stream), ctypes.byref(h)))
+    return Bins(h.value, graph)
+
+
+class Counts:
+    """Host copy of wedge_counts as numpy arrays."""
+
+    def __init__(self, c: CountsStruct):
+        self.raw = c
+        nb = c.n_bins
+        self.n_bins = nb
+        self.k_b = np.array(c.k_b[:nb], np.uint64)
+        self.q = np.array([list(c.q[i]) for i in range(nb)], np.uint64).reshape(nb, 4)
+        self.n_b = np.array(c.n_b[:nb], np.uint64)
+        self.p_b = np.array(c.p_b[:nb], np.uint64)
+        self.p_total = int(c.p_total)
+        self.k_global = int(c.k_global)
+        self.closed_global = int(c.closed_global)
+        self.stats = np.array([list(c.stats[i]) for i in range(STAT_BINS)], np.uint64)
+
+    def counts_matrix(self):
+        """(n_bins, 5) = (k_b, q0, q1, q2, q3), the oracle's layout."""
+        return np.concatenate([self.k_b[:, None], self.q], axis=1)
+
+
+def sample(graph: Graph, bins: Bins, seed: int, eps: float = 0.0, delta: float = 0.0, k_per_bin: int = 0,
+           k_global: int = 0, flags: int = 0, records=None, stream=None) -> Counts:
+    lib = load()
+    sp = SampleParams(seed, eps, delta, k_per_bin, k_global, flags, _ptr(records)[0] if records is not None else 0)
+    c = CountsStruct()
+    _check(lib.wedge_sample(graph.handle, bins.handle, ctypes.byref(sp), _stream_handle(stream), ctypes.byref(c)))
+    return Counts(c)
+
+
+def estimate(counts: Counts, delta: float) -> dict:
+    lib = load()
+    e = EstimatesStruct()
+    _check(lib.wedge_estimate(ctypes.byref(counts.raw), delta, ctypes.byref(e)))
+    nb = e.n_bins
+    return {"c_b": list(e.c_b[:nb]), "t_b": list(e.t_b[:nb]), "eps_b": list(e.eps_b[:nb]), "p": e.p_total,
+            "c_hat": e.c_hat, "t_hat": e.t_hat, "c_hat_global": e.c_hat_global, "t_hat_global": e.t_hat_global,
+            "eps_global": e.eps_global}
+
+
+def classify(graph: Graph, bins: Bins, v0, v1, v2, q, stream=None):
+    """Closure + class of given wedges (device arrays) into q (device uint8)."""
+    lib = load()
+    p0, k0 = _ptr(v0, np.int32)
+    p1, _ = _ptr(v1, np.int32)
+    p2, _ = _ptr(v2, np.int32)
+    pq, _ = _ptr(q, np.uint8)
+    n = int(k0.shape[0])
+    _check(lib.wedge_classify(graph.handle, bins.handle, n, p0, p1, p2, pq, _stream_handle(stream)))
+
+
+def hoeffding_k(eps: float, delta: float) -> int:
+    return int(load().wedge_hoeffding_k(eps, delta))
+
+
+def profile_enable(timing: bool = True):
+    load().wedge_profile_enable(1 if timing else 0)
+
+
+def profile_reset():
+    load().wedge_profile_reset()
+
+
+def profile_read() -> dict:
+    lib = load()
+    n = lib.wedge_profile_read(None, 0)
+    arr = (KernelStat * max(n, 1))()
+    n = lib.wedge_profile_read(arr, n)
+    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms)}
+            for i in range(n)}
+
+
+def trim():
+    _check(load().wedge_trim())

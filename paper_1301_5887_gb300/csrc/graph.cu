@@ -1,0 +1,306 @@
+// graph.cu — edge list -> CSR with degrees (wedge_graph_build).
+//
+// The paper's Phase 1a (Alg. Phase 1a) counts degrees by shuffling 2m
+// key-value pairs; here the same symmetrised pairs are packed into 64-bit keys
+// (u << b) | v, sorted by a device radix sort, deduplicated and cut into rows:
+//   1. expand: each input pair (u, v), u != v, emits (u,v) and (v,u); self-loops
+//      emit a sentinel that sorts last; ids outside [0, n) raise DERR_BAD_ID.
+//   2. sort: LSD radix over the 2b significant bits.
+//   3. dedup: adjacent-unique keys become adjacency entries (low b bits);
+//      warp-aggregated atomics count each row's length (the degree).
+//   4. offsets: exclusive scan of degrees into int64 row offsets.
+#include <algorithm>
+#include <atomic>
+
+#include "device.cuh"
+#include "internal.h"
+#include "runtime.h"
+
+namespace wedge {
+namespace {
+
+constexpr int DEDUP_THREADS = 256;
+constexpr int DEDUP_ITEMS = 16;
+constexpr int DEDUP_TILE = DEDUP_THREADS * DEDUP_ITEMS;
+
+__global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                                                int64_t m, int32_t n, uint32_t b, uint64_t sentinel,
+                                                ulonglong2* __restrict__ keys, uint32_t* err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const int32_t u = __ldcs(src + e), v = __ldcs(dst + e);
+    ulonglong2 kv;
+    if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
+      atomicOr(err, DERR_BAD_ID);
+      kv.x = kv.y = sentinel;
+    } else if (u == v) {
+      kv.x = kv.y = sentinel;
+    } else {
+      kv.x = ((uint64_t)u << b) | (uint64_t)v;
+      kv.y = ((uint64_t)v << b) | (uint64_t)u;
+    }
+    __stcs(keys + e, kv);
+  }
+}
+
+// Adjacent-unique of sorted keys -> adjacency entries and row lengths.
+__global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restrict__ keys, int64_t nkeys, uint32_t b,
+                                                         uint64_t sentinel, int32_t* __restrict__ adj,
+                                                         int32_t* __restrict__ deg, uint64_t* status,
+                                                         uint32_t* tile_ctr, uint32_t* err, int64_t* n_unique) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_wcount[DEDUP_THREADS / 32];
+  __shared__ uint64_t s_excl;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t wbase = tile * DEDUP_TILE + warp * (32 * DEDUP_ITEMS);
+  const uint64_t vmask = (1ULL << b) - 1ULL;
+
+  uint64_t k[DEDUP_ITEMS];
+  uint32_t bal[DEDUP_ITEMS];
+  uint32_t wcount = 0;
+  uint64_t prev_last = ~0ULL;  // key just before this warp's first item
+  if (lane == 0 && wbase > 0 && wbase - 1 < nkeys) prev_last = keys[wbase - 1];
+#pragma unroll
+  for (int i = 0; i < DEDUP_ITEMS; ++i) {
+    const int64_t idx = wbase + i * 32 + lane;
+    k[i] = idx < nkeys ? __ldcs(keys + idx) : sentinel;
+    const uint64_t up = __shfl_up_sync(FULL_MASK, k[i], 1);
+    const uint64_t from31 = __shfl_sync(FULL_MASK, k[i > 0 ? i - 1 : 0], 31);
+    const uint64_t prev = lane > 0 ? up : (i > 0 ? from31 : prev_last);
+    const bool f = (k[i] != sentinel) && (idx == 0 || k[i] != prev);
+    bal[i] = __ballot_sync(FULL_MASK, f);
+    wcount += __popc(bal[i]);
+  }
+  if (lane == 0) s_wcount[warp] = wcount;
+  __syncthreads();
+  if (tid == 0) {
+    uint64_t tile_total = 0;
+    for (int w = 0; w < DEDUP_THREADS / 32; ++w) tile_total += s_wcount[w];
+    uint64_t* st = status + tile;
+    uint64_t excl = 0;
+    if (tile == 0) {
+      st_relaxed(st, lb_pack(1, LB_INC, tile_total));
+    } else {
+      st_relaxed(st, lb_pack(1, LB_AGG, tile_total));
+      excl = lookback(status, tile, 1, 1, err);
+      st_relaxed(st, lb_pack(1, LB_INC, excl + tile_total));
+    }
+    s_excl = excl;
+    if ((tile + 1) * DEDUP_TILE >= nkeys) *n_unique = (int64_t)(excl + tile_total);
+  }
+  __syncthreads();
+  uint64_t pos = s_excl;
+  for (int w = 0; w < warp; ++w) pos += s_wcount[w];
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < DEDUP_ITEMS; ++i) {
+    const bool f = (bal[i] >> lane) & 1u;
+    const uint32_t u = f ? (uint32_t)(k[i] >> b) : 0xffffffffu;
+    if (f) adj[pos + __popc(bal[i] & lt)] = (int32_t)(k[i] & vmask);
+    const uint32_t peers = __match_any_sync(FULL_MASK, u);
+    if (f && (peers >> lane) == 1u) atomicAdd(deg + u, (int32_t)__popc(peers));  // highest lane of the run
+    pos += __popc(bal[i]);
+  }
+}
+
+int grid_stride_blocks(int64_t items, int threads) {
+  int64_t b = (items + threads - 1) / threads;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  if (b > cap) b = cap;
+  return b < 1 ? 1 : (int)b;
+}
+
+std::atomic<uint64_t> g_uid{1};
+
+struct BuildBuffers {
+  cudaStream_t s;
+  int32_t* src_dev = nullptr;
+  int32_t* dst_dev = nullptr;
+  uint64_t* keys_a = nullptr;
+  uint64_t* keys_b = nullptr;
+  void* scratch = nullptr;
+  uint32_t* derr = nullptr;     // [0] error bits, then padding
+  int64_t* scalars = nullptr;   // [0] n_unique, [1] max degree (int32 in low half)
+  ~BuildBuffers() {
+    dfree(src_dev, s);
+    dfree(dst_dev, s);
+    dfree(keys_a, s);
+    dfree(keys_b, s);
+    dfree(scratch, s);
+    dfree(derr, s);
+    dfree(scalars, s);
+  }
+};
+
+void free_graph(wedge_graph* g, cudaStream_t s) {
+  if (!g) return;
+  dfree(g->off, s);
+  dfree(g->adj, s);
+  dfree(g->deg, s);
+  delete g;
+}
+
+}  // namespace
+
+uint64_t next_uid() { return g_uid.fetch_add(1); }
+
+}  // namespace wedge
+
+using namespace wedge;
+
+#define BUILD_TRY(expr, what)                         \
+  do {                                                \
+    cudaError_t e__ = (expr);                         \
+    if (e__ != cudaSuccess) return bail(cuda_fail(e__, what)); \
+  } while (0)
+
+extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst, int64_t n_edges, int32_t n_vertices,
+                                          wedge_stream stream, wedge_graph** out) {
+  clear_error();
+  if (!out) return fail(WEDGE_EINVAL, "wedge_graph_build: out is NULL");
+  *out = nullptr;
+  if (n_edges < 0) return fail(WEDGE_EINVAL, "wedge_graph_build: n_edges < 0");
+  if (n_vertices < 1) return fail(WEDGE_EINVAL, "wedge_graph_build: n_vertices < 1");
+  if (n_edges > 0 && (!src || !dst)) return fail(WEDGE_EINVAL, "wedge_graph_build: NULL edge array");
+  if (n_edges > (int64_t(1) << 40)) return fail(WEDGE_EINVAL, "wedge_graph_build: n_edges > 2^40");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+  const uint32_t b = id_bits_for(n_vertices);
+  const uint64_t sentinel = (b * 2 >= 64) ? ~0ULL : ((1ULL << (2 * b)) - 1ULL);
+  const int64_t nkeys = 2 * n_edges;
+  BuildBuffers bb;
+  bb.s = s;
+  wedge_status st;
+
+  wedge_graph* g = new wedge_graph();
+  cudaGetDevice(&g->device);
+  g->uid = next_uid();
+  g->n = n_vertices;
+  g->id_bits = b;
+  g->n_input = n_edges;
+  g->off = nullptr;
+  g->adj = nullptr;
+  g->deg = nullptr;
+  auto bail = [&](wedge_status e) {
+    free_graph(g, s);
+    return e;
+  };
+
+  if ((st = dalloc_n(&bb.derr, 64, s, "wedge_graph_build")) != WEDGE_OK) return bail(st);
+  if ((st = dalloc_n(&bb.scalars, 4, s, "wedge_graph_build")) != WEDGE_OK) return bail(st);
+  if ((st = dalloc_n(&g->off, (size_t)n_vertices + 1, s, "wedge_graph_build: offsets")) != WEDGE_OK) return bail(st);
+  if ((st = dalloc_n(&g->deg, (size_t)n_vertices, s, "wedge_graph_build: degrees")) != WEDGE_OK) return bail(st);
+  if ((st = dalloc_n(&g->adj, (size_t)(nkeys > 0 ? nkeys : 1), s, "wedge_graph_build: adjacency")) != WEDGE_OK)
+    return bail(st);
+  BUILD_TRY(cudaMemsetAsync(bb.derr, 0, 64 * sizeof(uint32_t), s), "wedge_graph_build");
+  BUILD_TRY(cudaMemsetAsync(bb.scalars, 0, 4 * sizeof(int64_t), s), "wedge_graph_build");
+  BUILD_TRY(cudaMemsetAsync(g->deg, 0, (size_t)n_vertices * sizeof(int32_t), s), "wedge_graph_build");
+
+  if (n_edges > 0) {
+    const int32_t* s_in = src;
+    const int32_t* d_in = dst;
+    if (!device_accessible(src) || !device_accessible(dst)) {
+      // Host edge list: copy into device staging buffers on the caller's stream.
+      if ((st = dalloc_n(&bb.src_dev, (size_t)n_edges, s, "wedge_graph_build: staging")) != WEDGE_OK) return bail(st);
+      if ((st = dalloc_n(&bb.dst_dev, (size_t)n_edges, s, "wedge_graph_build: staging")) != WEDGE_OK) return bail(st);
+      cudaError_t e1 = cudaMemcpyAsync(bb.src_dev, src, (size_t)n_edges * 4, cudaMemcpyDefault, s);
+      cudaError_t e2 = cudaMemcpyAsync(bb.dst_dev, dst, (size_t)n_edges * 4, cudaMemcpyDefault, s);
+      if (e1 != cudaSuccess) return bail(cuda_fail(e1, "wedge_graph_build: copy src"));
+      if (e2 != cudaSuccess) return bail(cuda_fail(e2, "wedge_graph_build: copy dst"));
+      s_in = bb.src_dev;
+      d_in = bb.dst_dev;
+    }
+    if ((st = dalloc_n(&bb.keys_a, (size_t)nkeys, s, "wedge_graph_build: keys")) != WEDGE_OK) return bail(st);
+    if ((st = dalloc_n(&bb.keys_b, (size_t)nkeys, s, "wedge_graph_build: keys")) != WEDGE_OK) return bail(st);
+    const size_t scratch_bytes =
+        std::max(sort_scratch_bytes(nkeys, 2 * (int)b),
+                 std::max(scan_scratch_bytes(nkeys), scan_scratch_bytes(n_vertices)));
+    if ((st = dalloc(&bb.scratch, scratch_bytes, s, "wedge_graph_build: scratch")) != WEDGE_OK) return bail(st);
+
+    st = launch("expand_edges", s, [&] {
+      k_expand<<<grid_stride_blocks(n_edges, 256), 256, 0, s>>>(s_in, d_in, n_edges, n_vertices, b, sentinel,
+                                                                reinterpret_cast<ulonglong2*>(bb.keys_a), bb.derr);
+    });
+    if (st != WEDGE_OK) return bail(st);
+    // Staging buffers are no longer needed once the keys exist.
+    dfree(bb.src_dev, s);
+    dfree(bb.dst_dev, s);
+    bb.src_dev = bb.dst_dev = nullptr;
+
+    uint64_t* sorted = nullptr;
+    st = radix_sort_u64(bb.keys_a, bb.keys_b, nkeys, 2 * (int)b, bb.scratch, bb.derr, s, &sorted);
+    if (st != WEDGE_OK) return bail(st);
+
+    const int64_t tiles = (nkeys + DEDUP_TILE - 1) / DEDUP_TILE;
+    BUILD_TRY(cudaMemsetAsync(bb.scratch, 0, 256 + (size_t)tiles * sizeof(uint64_t), s), "wedge_graph_build");
+    uint32_t* ctr = static_cast<uint32_t*>(bb.scratch);
+    uint64_t* status = reinterpret_cast<uint64_t*>(static_cast<char*>(bb.scratch) + 256);
+    st = launch("dedup_rows", s, [&] {
+      k_dedup<<<(unsigned)tiles, DEDUP_THREADS, 0, s>>>(sorted, nkeys, b, sentinel, g->adj, g->deg, status, ctr,
+                                                        bb.derr, bb.scalars);
+    });
+    if (st != WEDGE_OK) return bail(st);
+    st = scan_i32_to_i64(g->deg, g->off, n_vertices, g->off + n_vertices,
+                         reinterpret_cast<int32_t*>(bb.scalars + 1), bb.scratch, bb.derr, s);
+    if (st != WEDGE_OK) return bail(st);
+  } else {
+    BUILD_TRY(cudaMemsetAsync(g->off, 0, ((size_t)n_vertices + 1) * sizeof(int64_t), s), "wedge_graph_build");
+  }
+
+  uint32_t herr = 0;
+  int64_t hs[2] = {0, 0};
+  BUILD_TRY(cudaMemcpyAsync(&herr, bb.derr, sizeof(herr), cudaMemcpyDeviceToHost, s), "wedge_graph_build");
+  BUILD_TRY(cudaMemcpyAsync(hs, bb.scalars, sizeof(hs), cudaMemcpyDeviceToHost, s), "wedge_graph_build");
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "wedge_graph_build"));
+  if (herr & DERR_BAD_ID) return bail(fail(WEDGE_EINVAL, "wedge_graph_build: a vertex id is outside [0, %d)", n_vertices));
+  if (herr & DERR_TIMEOUT) return bail(fail(WEDGE_ETIMEOUT, "wedge_graph_build: a look-back wait gave up"));
+  g->n_adj = hs[0];
+  g->max_degree = (int32_t)(hs[1] & 0xffffffff);
+  if (g->max_degree < 0) g->max_degree = 0;
+  *out = g;
+  return WEDGE_OK;
+}
+
+#undef BUILD_TRY
+
+extern "C" void wedge_graph_free(wedge_graph* g) {
+  if (!g) return;
+  cudaDeviceSynchronize();
+  free_graph(g, nullptr);
+}
+
+extern "C" wedge_status wedge_graph_get_info(const wedge_graph* g, wedge_graph_info* out) {
+  clear_error();
+  if (!g || !out) return fail(WEDGE_EINVAL, "wedge_graph_get_info: NULL argument");
+  out->n_vertices = g->n;
+  out->id_bits = (int32_t)g->id_bits;
+  out->n_adj = g->n_adj;
+  out->n_input_edges = g->n_input;
+  out->max_degree = g->max_degree;
+  out->off = g->off;
+  out->adj = g->adj;
+  out->deg = g->deg;
+  return WEDGE_OK;
+}
+
+extern "C" wedge_status wedge_graph_copy(const wedge_graph* g, int64_t* off, int32_t* adj, int32_t* deg,
+                                         wedge_stream stream) {
+  clear_error();
+  if (!g) return fail(WEDGE_EINVAL, "wedge_graph_copy: NULL graph");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (off)
+    WEDGE_CUDA_TRY(cudaMemcpyAsync(off, g->off, ((size_t)g->n + 1) * sizeof(int64_t), cudaMemcpyDefault, s),
+                   "wedge_graph_copy");
+  if (adj && g->n_adj > 0)
+    WEDGE_CUDA_TRY(cudaMemcpyAsync(adj, g->adj, (size_t)g->n_adj * sizeof(int32_t), cudaMemcpyDefault, s),
+                   "wedge_graph_copy");
+  if (deg)
+    WEDGE_CUDA_TRY(cudaMemcpyAsync(deg, g->deg, (size_t)g->n * sizeof(int32_t), cudaMemcpyDefault, s),
+                   "wedge_graph_copy");
+  WEDGE_CUDA_TRY(cudaStreamSynchronize(s), "wedge_graph_copy");
+  return WEDGE_OK;
+}

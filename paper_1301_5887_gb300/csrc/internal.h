@@ -1,0 +1,52 @@
+// internal.h — library-private handle layouts and cross-file entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/wedge.h"
+
+struct wedge_graph {
+  int device;
+  uint64_t uid;
+  int32_t n;
+  uint32_t id_bits;
+  int64_t n_adj;
+  int64_t n_input;
+  int32_t max_degree;
+  int64_t* off;  // n + 1
+  int32_t* adj;  // n_adj (allocation may be larger)
+  int32_t* deg;  // n
+};
+
+struct wedge_bins {
+  int device;
+  uint64_t graph_uid;
+  uint32_t pow2;            // tau = 1, omega = 2
+  wedge_bins_info info;     // host copy; info.L / info.W point at L / W
+  int32_t* L;               // n_wedge_vertices
+  uint64_t* W;              // n_wedge_vertices + 1
+  uint64_t* lo_dev;         // bin table: n_bins entries
+};
+
+namespace wedge {
+
+// Sort-scratch size and sort (sort.cu).
+size_t sort_scratch_bytes(int64_t n, int bits);
+wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, void* scratch, uint32_t* derr,
+                            cudaStream_t s, uint64_t** sorted);
+
+// Exclusive scans with decoupled look-back (scan.cu).
+size_t scan_scratch_bytes(int64_t n);
+// out[i] = sum in[0..i) for i < n; if total != nullptr, *total = sum of all.
+// If maxv != nullptr, atomicMax(maxv, max input) (inputs interpreted as int32).
+wedge_status scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, int64_t* total, int32_t* maxv, void* scratch,
+                             uint32_t* derr, cudaStream_t s);
+wedge_status scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, void* scratch, uint32_t* derr,
+                             cudaStream_t s);
+wedge_status scan_u64_to_u64(const uint64_t* in, uint64_t* out, int64_t n, void* scratch, uint32_t* derr,
+                             cudaStream_t s);
+
+uint64_t next_uid();
+
+}  // namespace wedge

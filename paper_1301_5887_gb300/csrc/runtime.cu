@@ -1,0 +1,245 @@
+// runtime.cu — error strings, memory pool, launch accounting, timing.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "runtime.h"
+
+namespace wedge {
+
+namespace {
+thread_local char g_err[512] = "";
+
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+struct KStat {
+  uint64_t launches = 0;
+  double total_ms = 0.0;
+};
+struct Pending {
+  std::string name;
+  cudaEvent_t e0, e1;
+};
+std::mutex g_prof_mu;
+bool g_timing = false;
+std::map<std::string, KStat> g_stats;
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_free_events;
+
+cudaEvent_t get_event() {
+  if (!g_free_events.empty()) {
+    cudaEvent_t e = g_free_events.back();
+    g_free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+cudaMemPool_t pool_for_current(cudaError_t* err) {
+  int dev = 0;
+  *err = cudaGetDevice(&dev);
+  if (*err != cudaSuccess) return nullptr;
+  if (dev < 0 || dev >= kMaxDevices) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    *err = cudaMemPoolCreate(&p, &props);
+    if (*err != cudaSuccess) return nullptr;
+    uint64_t keep = UINT64_MAX;  // keep freed blocks cached for the next call
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = p;
+  }
+  return g_pool[dev];
+}
+}  // namespace
+
+wedge_status fail(wedge_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+void clear_error() { g_err[0] = '\0'; }
+
+wedge_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(WEDGE_ENOMEM, "%s: out of device memory", what);
+  }
+  return fail(WEDGE_ECUDA, "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+}
+
+wedge_status dalloc(void** p, size_t bytes, cudaStream_t s, const char* what) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 256;
+  cudaError_t err = cudaSuccess;
+  cudaMemPool_t pool = pool_for_current(&err);
+  if (!pool) return cuda_fail(err, what);
+  err = cudaMallocFromPoolAsync(p, bytes, pool, s);
+  if (err != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    if (err == cudaErrorMemoryAllocation)
+      return fail(WEDGE_ENOMEM, "%s: cannot allocate %zu bytes of device memory", what, bytes);
+    return cuda_fail(err, what);
+  }
+  return WEDGE_OK;
+}
+
+void dfree(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+wedge_status trim_pool() {
+  cudaError_t err = cudaSuccess;
+  cudaMemPool_t pool = pool_for_current(&err);
+  if (!pool) return cuda_fail(err, "wedge_trim");
+  WEDGE_CUDA_TRY(cudaDeviceSynchronize(), "wedge_trim");
+  WEDGE_CUDA_TRY(cudaMemPoolTrimTo(pool, 0), "wedge_trim");
+  return WEDGE_OK;
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 148;
+  return sms;
+}
+
+LaunchMark launch_begin(const char* name, cudaStream_t s) {
+  LaunchMark m{name, s, nullptr};
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_stats[name].launches += 1;
+  if (g_timing) {
+    m.start = get_event();
+    if (m.start) cudaEventRecord(m.start, s);
+  }
+  return m;
+}
+
+wedge_status launch_end(const LaunchMark& m) {
+  cudaError_t e = cudaGetLastError();
+  if (m.start) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEvent_t e1 = get_event();
+    if (e1) {
+      cudaEventRecord(e1, m.stream);
+      g_pending.push_back(Pending{m.name, m.start, e1});
+    } else {
+      g_free_events.push_back(m.start);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, m.name);
+  return WEDGE_OK;
+}
+
+bool device_accessible(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+uint32_t id_bits_for(int64_t n) {
+  uint32_t b = 1;
+  while (b < 62 && (int64_t(1) << b) < n) ++b;
+  return b;
+}
+
+}  // namespace wedge
+
+using namespace wedge;
+
+extern "C" {
+
+const char* wedge_last_error(void) { return g_err; }
+
+uint32_t wedge_version(void) { return 0x000100u; }
+
+int wedge_abi_sizes(uint64_t* sizes, int cap) {
+  const uint64_t v[7] = {sizeof(wedge_graph_info), sizeof(wedge_bins_info), sizeof(wedge_sample_params),
+                         sizeof(wedge_record),     sizeof(wedge_counts),    sizeof(wedge_estimates),
+                         sizeof(wedge_kernel_stat)};
+  for (int i = 0; i < 7 && i < cap && sizes; ++i) sizes[i] = v[i];
+  return 7;
+}
+
+const char* wedge_status_str(wedge_status st) {
+  switch (st) {
+    case WEDGE_OK: return "WEDGE_OK";
+    case WEDGE_EINVAL: return "WEDGE_EINVAL";
+    case WEDGE_ENOMEM: return "WEDGE_ENOMEM";
+    case WEDGE_ECUDA: return "WEDGE_ECUDA";
+    case WEDGE_ETIMEOUT: return "WEDGE_ETIMEOUT";
+    case WEDGE_EOVERFLOW: return "WEDGE_EOVERFLOW";
+  }
+  return "WEDGE_UNKNOWN";
+}
+
+void wedge_profile_enable(int enable_timing) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_timing = enable_timing != 0;
+}
+
+void wedge_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& p : g_pending) {
+    cudaEventSynchronize(p.e1);
+    g_free_events.push_back(p.e0);
+    g_free_events.push_back(p.e1);
+  }
+  g_pending.clear();
+  g_stats.clear();
+}
+
+int wedge_profile_read(wedge_kernel_stat* out, int cap) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& p : g_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.e1) == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess)
+      g_stats[p.name].total_ms += ms;
+    g_free_events.push_back(p.e0);
+    g_free_events.push_back(p.e1);
+  }
+  g_pending.clear();
+  int i = 0;
+  for (auto& kv : g_stats) {
+    if (out && i < cap) {
+      memset(&out[i], 0, sizeof(out[i]));
+      strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
+      out[i].launches = kv.second.launches;
+      out[i].total_ms = kv.second.total_ms;
+    }
+    ++i;
+  }
+  return i;
+}
+
+wedge_status wedge_trim(void) {
+  clear_error();
+  return trim_pool();
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// scan.cu — single-pass exclusive prefix sums with decoupled look-back
+// (Merrill and Garland, "Single-pass parallel prefix scan with decoupled
+// look-back", NVIDIA TR 2016). Used for CSR row offsets and bin positions.
+//
+// One CTA scans a tile of 4096 items: a warp-striped coalesced load into
+// shared memory, a per-thread sequential sum over 16 consecutive items, a
+// block scan of thread sums, then one look-back by thread 0 to get the
+// tile's global prefix. Tiles are claimed in launch order from an atomic
+// ticket, so every wait is on a tile that is already running.
+#include "device.cuh"
+#include "internal.h"
+#include "runtime.h"
+
+namespace wedge {
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
+
+template <typename Tin, typename Tout>
+__global__ __launch_bounds__(SCAN_THREADS) void k_scan_excl(const Tin* __restrict__ in, Tout* __restrict__ out,
+                                                            int64_t n, uint64_t* status, uint32_t* tile_ctr,
+                                                            uint32_t* err, Tout* total, int32_t* maxv) {
+  __shared__ Tout s_buf[SCAN_TILE + SCAN_TILE / 32];
+  __shared__ Tout s_wsum[SCAN_THREADS / 32];
+  __shared__ uint32_t s_tile;
+  __shared__ Tout s_excl;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t tbase = tile * SCAN_TILE;
+  int32_t local_max = INT32_MIN;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    const int idx = i * SCAN_THREADS + tid;
+    const int64_t g = tbase + idx;
+    Tout v = 0;
+    if (g < n) {
+      const Tin x = in[g];
+      v = (Tout)x;
+      if (maxv) local_max = max(local_max, (int32_t)x);
+    }
+    s_buf[pad(idx)] = v;
+  }
+  __syncthreads();
+  Tout item[SCAN_ITEMS];
+  Tout sum = 0;
+#pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    item[j] = s_buf[pad(tid * SCAN_ITEMS + j)];
+    sum += item[j];
+  }
+  // block exclusive scan of per-thread sums
+  Tout incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const Tout y = __shfl_up_sync(FULL_MASK, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  if (maxv) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local_max = max(local_max, __shfl_xor_sync(FULL_MASK, local_max, o));
+    if (lane == 0 && local_max != INT32_MIN) atomicMax(maxv, local_max);
+  }
+  __syncthreads();
+  Tout wpre = 0, tile_total = 0;
+#pragma unroll
+  for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+    if (w < warp) wpre += s_wsum[w];
+    tile_total += s_wsum[w];
+  }
+  if (tid == 0) {
+    uint64_t* st = status + tile;
+    Tout excl = 0;
+    if (tile == 0) {
+      st_relaxed(st, lb_pack(1, LB_INC, (uint64_t)tile_total));
+    } else {
+      st_relaxed(st, lb_pack(1, LB_AGG, (uint64_t)tile_total));
+      excl = (Tout)lookback(status, tile, 1, 1, err);
+      st_relaxed(st, lb_pack(1, LB_INC, (uint64_t)(excl + tile_total)));
+    }
+    s_excl = excl;
+    if (total && tbase + SCAN_TILE >= n) *total = excl + tile_total;
+  }
+  __syncthreads();
+  Tout run = s_excl + wpre + incl - sum;
+#pragma unroll
+  for (int j = 0; j < SCAN_ITEMS; ++j) {
+    s_buf[pad(tid * SCAN_ITEMS + j)] = run;
+    run += item[j];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    const int idx = i * SCAN_THREADS + tid;
+    const int64_t g = tbase + idx;
+    if (g < n) out[g] = s_buf[pad(idx)];
+  }
+}
+
+template <typename Tin, typename Tout>
+wedge_status run_scan(const Tin* in, Tout* out, int64_t n, Tout* total, int32_t* maxv, void* scratch, uint32_t* derr,
+                      cudaStream_t s, const char* name) {
+  if (n <= 0) {
+    if (total) WEDGE_CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(Tout), s), name);
+    return WEDGE_OK;
+  }
+  const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (tiles > (int64_t)UINT32_MAX) return fail(WEDGE_EINVAL, "%s: too many items (%lld)", name, (long long)n);
+  uint32_t* ctr = static_cast<uint32_t*>(scratch);
+  uint64_t* status = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + 256);
+  WEDGE_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256 + (size_t)tiles * sizeof(uint64_t), s), name);
+  return launch(name, s, [&] {
+    k_scan_excl<Tin, Tout><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, status, ctr, derr, total, maxv);
+  });
+}
+
+}  // namespace
+
+size_t scan_scratch_bytes(int64_t n) {
+  const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  return 256 + (size_t)(tiles + 1) * sizeof(uint64_t);
+}
+
+wedge_status scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, int64_t* total, int32_t* maxv, void* scratch,
+                             uint32_t* derr, cudaStream_t s) {
+  return run_scan<int32_t, int64_t>(in, out, n, total, maxv, scratch, derr, s, "scan_degrees");
+}
+
+wedge_status scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, void* scratch, uint32_t* derr,
+                             cudaStream_t s) {
+  return run_scan<uint32_t, int64_t>(in, out, n, nullptr, nullptr, scratch, derr, s, "scan_bin_counts");
+}
+
+wedge_status scan_u64_to_u64(const uint64_t* in, uint64_t* out, int64_t n, void* scratch, uint32_t* derr,
+                             cudaStream_t s) {
+  return run_scan<uint64_t, uint64_t>(in, out, n, nullptr, nullptr, scratch, derr, s, "scan_bin_wedges");
+}
+
+}  // namespace wedge
