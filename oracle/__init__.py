@@ -65,7 +65,7 @@ def _L():
         _lib.oracle_classify.restype = ctypes.c_int
         _lib.oracle_exact.argtypes = [i32, P, P, u32, u64, i32, P, P]
         _lib.oracle_exact.restype = u64
-        _lib.oracle_rows_kronecker.argtypes = [u32, i64, dbl, dbl, dbl, u64, ctypes.c_int, i64, P, P, P, P]
+        _lib.oracle_rows_kronecker.argtypes = [u32, i64, dbl, dbl, dbl, u64, ctypes.c_int, i64, P, i64, P, P]
         _lib.oracle_rows_kronecker.restype = i64
     return _lib
 
@@ -206,20 +206,23 @@ def exact(off, adj, tau: int, omega: int):
     return {"t": t, "t_i": t_i[:n], "pbq": pbq, "n_b": bb["n_b"], "p_b": bb["p_b"]}
 
 
-def rows_kronecker(scale: int, n_edges: int, a: float, b: float, c: float, seed: int, permute: bool, query):
+def rows_kronecker(scale: int, n_edges: int, a: float, b: float, c: float, seed: int, permute: bool, query,
+                   cap: int = 1 << 24):
     """Exact neighbour sets of the query vertices of a generated Kronecker graph,
     by one scan over its generated edges. Returns {vertex: ascending int32 array}."""
     q = np.unique(_c(query, np.int32))
     nq = q.shape[0]
-    row_off = np.zeros(nq + 1, np.int64)
-    cap = _L().oracle_rows_kronecker(scale, n_edges, a, b, c, seed, int(permute), nq, _p(q), _p(row_off),
-                                     ctypes.c_void_p(0), ctypes.c_void_p(0))
-    if cap < 0:
-        raise MemoryError("oracle_rows_kronecker failed")
-    nbuf = np.zeros(max(int(cap), 1), np.int32)
-    row_len = np.zeros(nq, np.int64)
-    rc = _L().oracle_rows_kronecker(scale, n_edges, a, b, c, seed, int(permute), nq, _p(q), _p(row_off), _p(nbuf),
-                                    _p(row_len))
-    if rc != 0:
-        raise MemoryError("oracle_rows_kronecker failed")
-    return {int(v): nbuf[row_off[i]: row_off[i] + row_len[i]].copy() for i, v in enumerate(q)}
+    while True:
+        pq = np.zeros(cap, np.int32)
+        pn = np.zeros(cap, np.int32)
+        total = int(_L().oracle_rows_kronecker(scale, n_edges, a, b, c, seed, int(permute), nq, _p(q), cap, _p(pq),
+                                               _p(pn)))
+        if total <= cap:
+            break
+        cap = total
+    key = pq[:total].astype(np.int64) << 32 | pn[:total].astype(np.int64)
+    key = np.unique(key)
+    qi = (key >> 32).astype(np.int64)
+    nb = (key & 0xFFFFFFFF).astype(np.int32)
+    bounds = np.searchsorted(qi, np.arange(nq + 1))
+    return {int(v): nb[bounds[i]:bounds[i + 1]].copy() for i, v in enumerate(q)}

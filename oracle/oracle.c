@@ -489,47 +489,21 @@ static int64_t find_sorted(const int32_t* q, int64_t nq, int32_t x) {
   return (lo < nq && q[lo] == x) ? lo : -1;
 }
 
-/* The neighbour set of each query vertex (ascending, distinct ids) in the
+/* Neighbours of the query vertices (ascending, distinct ids in q) in the
  * undirected simple graph of Kronecker edges [0, n_edges), found by one scan
- * of the generated edges (edge set semantics as in oracle_csr). Two calls:
- * with nb == NULL it fills row_off[nq+1] with an upper bound layout and
- * returns the total capacity; with nb it fills rows and sets row_len[i]. */
+ * of the generated edges: every edge (u, v), u != v, with u in q yields the
+ * pair (index of u in q, v), and with v in q the pair (index of v, u).
+ * Pairs are written to pair_q / pair_nb while fewer than cap; the return
+ * value is the total number of pairs (repeats included; the caller sorts and
+ * drops repeats, since a row is a set). */
 OR_EXPORT int64_t oracle_rows_kronecker(uint32_t scale, int64_t n_edges, double a, double b, double c, uint64_t seed,
-                                        int permute, int64_t nq, const int32_t* q, int64_t* row_off, int32_t* nb,
-                                        int64_t* row_len) {
+                                        int permute, int64_t nq, const int32_t* q, int64_t cap, int32_t* pair_q,
+                                        int32_t* pair_nb) {
   const gg_rmat_thresholds th = gg_rmat_make(a, b, c);
   const uint64_t n = 1ULL << scale;
   const gg_perm perm = gg_perm_make(n, seed);
   const uint64_t es = gg_stream_seed(seed, GG_STREAM_EDGES);
-  if (!nb) {
-    int64_t* cnt = (int64_t*)calloc((size_t)nq + 1, sizeof(int64_t));
-    if (!cnt) return -2;
-#pragma omp parallel for schedule(static)
-    for (int64_t e = 0; e < n_edges; ++e) {
-      uint64_t u, v;
-      gg_rmat_edge(&th, scale, es, (uint64_t)e, &u, &v);
-      if (permute) {
-        u = gg_perm_apply(&perm, u);
-        v = gg_perm_apply(&perm, v);
-      }
-      if (u == v) continue;
-      const int64_t iu = find_sorted(q, nq, (int32_t)u), iv = find_sorted(q, nq, (int32_t)v);
-      if (iu >= 0) {
-#pragma omp atomic
-        cnt[iu] += 1;
-      }
-      if (iv >= 0) {
-#pragma omp atomic
-        cnt[iv] += 1;
-      }
-    }
-    row_off[0] = 0;
-    for (int64_t i = 0; i < nq; ++i) row_off[i + 1] = row_off[i] + cnt[i];
-    free(cnt);
-    return row_off[nq];
-  }
-  int64_t* fill = (int64_t*)calloc((size_t)nq + 1, sizeof(int64_t));
-  if (!fill) return -2;
+  int64_t total = 0;
 #pragma omp parallel for schedule(static)
   for (int64_t e = 0; e < n_edges; ++e) {
     uint64_t u, v;
@@ -543,29 +517,21 @@ OR_EXPORT int64_t oracle_rows_kronecker(uint32_t scale, int64_t n_edges, double 
     if (iu >= 0) {
       int64_t slot;
 #pragma omp atomic capture
-      slot = fill[iu]++;
-      nb[row_off[iu] + slot] = (int32_t)v;
+      slot = total++;
+      if (slot < cap) {
+        pair_q[slot] = (int32_t)iu;
+        pair_nb[slot] = (int32_t)v;
+      }
     }
     if (iv >= 0) {
       int64_t slot;
 #pragma omp atomic capture
-      slot = fill[iv]++;
-      nb[row_off[iv] + slot] = (int32_t)u;
+      slot = total++;
+      if (slot < cap) {
+        pair_q[slot] = (int32_t)iv;
+        pair_nb[slot] = (int32_t)u;
+      }
     }
   }
-  for (int64_t i = 0; i < nq; ++i) {
-    int32_t* r = nb + row_off[i];
-    const int64_t len = fill[i];
-    /* sort then drop repeats: the row is a set */
-    uint64_t* tmp = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(len + 1));
-    for (int64_t x = 0; x < len; ++x) tmp[x] = (uint64_t)(uint32_t)r[x];
-    qsort(tmp, (size_t)len, sizeof(uint64_t), cmp_u64);
-    int64_t m = 0;
-    for (int64_t x = 0; x < len; ++x)
-      if (x == 0 || tmp[x] != tmp[x - 1]) r[m++] = (int32_t)tmp[x];
-    row_len[i] = m;
-    free(tmp);
-  }
-  free(fill);
-  return 0;
+  return total;
 }
