@@ -247,6 +247,33 @@ WEDGE_API wedge_status wedge_classify(const wedge_graph* g, const wedge_bins* b,
                             const int32_t* v1, const int32_t* v2, uint8_t* q, wedge_stream s);
 
 /* --------------------------------------------------------------------------
+ * Allocation-free CSR row offsets. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory — code running
+ * inside a host framework that has already reserved nearly all of the GPU's
+ * memory for its own pool (so a cudaMalloc would fail), plug-in or operator
+ * callbacks whose host API forbids allocation on the execution path, and
+ * latency-bound loops that cannot take the implicit device synchronisation
+ * of cudaMalloc/cudaFree. It computes the same row offsets as step 4 of
+ * wedge_graph_build, off[i] = deg[0] + ... + deg[i-1] for i = 0..n (so
+ * off[n] is the total), with the same single-pass scan kernel, but keeps the
+ * kernel's look-back scratch in a fixed 1 MiB device array inside the
+ * library instead of allocating it.
+ *   deg: device, n int32 degrees (>= 0); off: device, n + 1 int64 outputs.
+ *   Returns after synchronising s. Allocates no device memory and calls no
+ *   allocating routine.
+ *   The scratch array is resident on every GPU that loads the library until
+ *   the process exits. The first call on a device looks up the array's device
+ *   address; make that first call before any stream capture on that device.
+ *   All calls share the one array, so calls that overlap on the GPU (other
+ *   host threads, other streams) race and must be serialised by the caller.
+ *   Errors: EINVAL if n < 0, a pointer is NULL, or n exceeds
+ *   WEDGE_NOALLOC_MAX_VERTICES; ECUDA; ETIMEOUT (a bounded look-back wait
+ *   gave up).
+ * ------------------------------------------------------------------------ */
+#define WEDGE_NOALLOC_MAX_VERTICES 536870912LL /* 131072 tiles x 4096 degrees */
+WEDGE_API wedge_status wedge_degree_offsets_noalloc(const int32_t* deg, int64_t n, int64_t* off, wedge_stream s);
+
+/* --------------------------------------------------------------------------
  * Tracing: per-kernel device time from CUDA events recorded on the launching
  * stream around each launch (when enabled), and launch counts (always).
  * ------------------------------------------------------------------------ */

@@ -99,7 +99,8 @@ _STRUCTS = [GraphInfo, BinsInfo, SampleParams, Record, CountsStruct, EstimatesSt
 EXPORTS = ["wedge_status_str", "wedge_last_error", "wedge_version", "wedge_abi_sizes", "wedge_graph_build",
            "wedge_graph_free", "wedge_graph_get_info", "wedge_graph_copy", "wedge_bin", "wedge_bins_free",
            "wedge_bins_get_info", "wedge_bins_copy", "wedge_sample", "wedge_hoeffding_k", "wedge_estimate", "wedge_classify",
-           "wedge_profile_enable", "wedge_profile_reset", "wedge_profile_read", "wedge_trim"]
+           "wedge_profile_enable", "wedge_profile_reset", "wedge_profile_read", "wedge_trim",
+           "wedge_degree_offsets_noalloc"]
 
 _lib = None
 
@@ -140,6 +141,7 @@ def load():
         "wedge_profile_reset": ([], None),
         "wedge_profile_read": ([P, ctypes.c_int], ctypes.c_int),
         "wedge_trim": ([], st),
+        "wedge_degree_offsets_noalloc": ([P, i64, P, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -344,6 +346,18 @@ def classify(graph: Graph, bins: Bins, v0, v1, v2, q, stream=None):
     pq, _ = _ptr(q, np.uint8)
     n = int(k0.shape[0])
     _check(lib.wedge_classify(graph.handle, bins.handle, n, p0, p1, p2, pq, _stream_handle(stream)))
+
+
+NOALLOC_MAX_VERTICES = 536870912
+
+
+def degree_offsets_noalloc(deg, off, stream=None):
+    """Row offsets off[0..n] from device degrees deg[0..n) without any device
+    allocation (wedge_degree_offsets_noalloc); off must hold n + 1 int64."""
+    lib = load()
+    pd, kd = _ptr(deg, np.int32)
+    po, _ = _ptr(off, np.int64)
+    _check(lib.wedge_degree_offsets_noalloc(pd, int(kd.shape[0]), po, _stream_handle(stream)))
 
 
 def hoeffding_k(eps: float, delta: float) -> int:

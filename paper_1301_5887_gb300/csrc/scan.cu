@@ -7,6 +7,8 @@
 // block scan of thread sums, then one look-back by thread 0 to get the
 // tile's global prefix. Tiles are claimed in launch order from an atomic
 // ticket, so every wait is on a tile that is already running.
+#include <mutex>
+
 #include "device.cuh"
 #include "internal.h"
 #include "runtime.h"
@@ -142,4 +144,83 @@ wedge_status scan_u64_to_u64(const uint64_t* in, uint64_t* out, int64_t n, void*
   return run_scan<uint64_t, uint64_t>(in, out, n, nullptr, nullptr, scratch, derr, s, "scan_bin_wedges");
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free row offsets (wedge_degree_offsets_noalloc).
+//
+// For callers that must not allocate device memory: the look-back scratch
+// of the scan lives in one fixed file-scope device array instead of the
+// library's pool. Layout: [tile ticket: 4 B][pad][error word at +64][pad to
+// 256 B][one look-back word per 4096-degree tile].
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t NOALLOC_MAX_TILES = 131072;  // 1 MiB of look-back words
+constexpr size_t NOALLOC_HEADER = 256;
+static_assert((int64_t)WEDGE_NOALLOC_MAX_VERTICES == NOALLOC_MAX_TILES * SCAN_TILE,
+              "header maximum must match the scratch size");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_HEADER + NOALLOC_MAX_TILES * sizeof(uint64_t)];
+
+constexpr int kNoallocDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoallocDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code cannot use the symbol itself as a device pointer).
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoallocDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
 }  // namespace wedge
+
+using namespace wedge;
+
+extern "C" wedge_status wedge_degree_offsets_noalloc(const int32_t* deg, int64_t n, int64_t* off,
+                                                     wedge_stream stream) {
+  clear_error();
+  if (n < 0) return fail(WEDGE_EINVAL, "wedge_degree_offsets_noalloc: n < 0");
+  if (!off || (n > 0 && !deg)) return fail(WEDGE_EINVAL, "wedge_degree_offsets_noalloc: NULL array");
+  if (n > (int64_t)WEDGE_NOALLOC_MAX_VERTICES)
+    return fail(WEDGE_EINVAL, "wedge_degree_offsets_noalloc: n = %lld exceeds the maximum of %lld vertices",
+                (long long)n, (long long)WEDGE_NOALLOC_MAX_VERTICES);
+  void* base = nullptr;
+  cudaError_t e = noalloc_scratch(&base);
+  if (e != cudaSuccess) return cuda_fail(e, "wedge_degree_offsets_noalloc: scratch address");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    WEDGE_CUDA_TRY(cudaMemsetAsync(off, 0, sizeof(int64_t), s), "wedge_degree_offsets_noalloc");
+    WEDGE_CUDA_TRY(cudaStreamSynchronize(s), "wedge_degree_offsets_noalloc");
+    return WEDGE_OK;
+  }
+  const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  unsigned char* b = static_cast<unsigned char*>(base);
+  uint32_t* ctr = reinterpret_cast<uint32_t*>(b);
+  uint32_t* err = reinterpret_cast<uint32_t*>(b + 64);
+  uint64_t* status = reinterpret_cast<uint64_t*>(b + NOALLOC_HEADER);
+  // The array keeps the previous call's contents: clear the ticket, the
+  // error word and this call's look-back words.
+  WEDGE_CUDA_TRY(cudaMemsetAsync(b, 0, NOALLOC_HEADER + (size_t)tiles * sizeof(uint64_t), s),
+                 "wedge_degree_offsets_noalloc");
+  k_scan_excl<int32_t, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(deg, off, n, status, ctr, err, off + n,
+                                                                           nullptr);
+  WEDGE_CUDA_TRY(cudaGetLastError(), "wedge_degree_offsets_noalloc: launch");
+  uint32_t herr = 0;
+  WEDGE_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s),
+                 "wedge_degree_offsets_noalloc");
+  WEDGE_CUDA_TRY(cudaStreamSynchronize(s), "wedge_degree_offsets_noalloc");
+  if (herr & DERR_TIMEOUT) return fail(WEDGE_ETIMEOUT, "wedge_degree_offsets_noalloc: a look-back wait gave up");
+  return WEDGE_OK;
+}
