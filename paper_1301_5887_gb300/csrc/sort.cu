@@ -3,10 +3,11 @@
 // One-sweep scheme (Adinets and Merrill, "Onesweep: a faster least
 // significant digit radix sort for GPUs", 2022): one upfront pass builds the
 // 256-bin histograms of every digit position; each digit pass then reads and
-// writes the keys once. A CTA ranks its 4096-key tile with warp-level
-// match-based multisplit, publishes its per-digit counts with decoupled
-// look-back, and scatters the keys through shared memory so that runs of
-// equal digits are written contiguously.
+// writes the keys once. A 256-thread CTA counts its 4096-key tile's digits
+// per warp and publishes them for decoupled look-back before ranking, ranks
+// the keys stably with a warp-level multisplit (peer masks from digit-bit
+// ballots) straight into shared memory in digit order, and writes runs of
+// equal digits contiguously.
 //
 // Only the low `bits` bits are sorted (2 x id bits for packed (u, v) keys),
 // 8 bits per pass; stable, so the result is sorted by the full bit range.
@@ -22,17 +23,27 @@ constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
 constexpr int SORT_ITEMS = 16;
-constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 4096 keys
 constexpr int MAX_PASSES = 8;
+constexpr int HIST_THREADS = 256;
 
-__global__ __launch_bounds__(256) void k_sort_hist(const uint64_t* __restrict__ keys, int64_t n, int passes,
-                                                   unsigned long long* __restrict__ hist) {
+__global__ __launch_bounds__(HIST_THREADS) void k_sort_hist(const uint64_t* __restrict__ keys, int64_t n, int passes,
+                                                            unsigned long long* __restrict__ hist) {
   __shared__ uint32_t sh[MAX_PASSES * RADIX];
   for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) sh[i] = 0;
   __syncthreads();
+  const int64_t n2 = n >> 1;  // pairs of keys, 16-byte loads
+  const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(keys);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint64_t k = __ldcs(keys + i);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+    const ulonglong2 kk = __ldcs(k2 + i);
+    for (int p = 0; p < passes; ++p) {
+      atomicAdd(&sh[p * RADIX + (uint32_t)((kk.x >> (RADIX_BITS * p)) & (RADIX - 1))], 1u);
+      atomicAdd(&sh[p * RADIX + (uint32_t)((kk.y >> (RADIX_BITS * p)) & (RADIX - 1))], 1u);
+    }
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const uint64_t k = keys[n - 1];
     for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * RADIX + (uint32_t)((k >> (RADIX_BITS * p)) & (RADIX - 1))], 1u);
   }
   __syncthreads();
@@ -70,100 +81,138 @@ struct PassArgs {
   uint32_t* err;
 };
 
-__global__ __launch_bounds__(SORT_THREADS) void k_sort_pass(PassArgs a) {
-  __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_whist[SORT_WARPS][RADIX + 1];  // +1: slot for padding items
-  __shared__ uint32_t s_dstart[RADIX];
-  __shared__ uint64_t s_goff[RADIX];
-  __shared__ uint32_t s_wsum[SORT_WARPS];
-  __shared__ uint64_t s_keys[SORT_TILE];
+struct PassSmem {
+  uint64_t keys[SORT_TILE];             // tile in digit order
+  uint64_t goff[RADIX];                 // global index - local position, per digit
+  uint32_t whist[SORT_WARPS][RADIX];    // per-warp digit counts, then running bases
+  uint32_t dstart[RADIX];               // tile-local start of each digit
+  uint32_t wsum[SORT_WARPS];
+  uint32_t tile;
+};
+constexpr size_t PASS_SMEM = sizeof(PassSmem);
 
+// Peer mask of this lane's digit d (0..RADIX, RADIX = no key): the lanes of
+// the warp holding the same value, from one ballot per digit bit.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
+  uint32_t peers = __ballot_sync(FULL_MASK, d >> RADIX_BITS);
+  if (!(d >> RADIX_BITS)) peers = ~peers;
+#pragma unroll
+  for (int b = 0; b < RADIX_BITS; ++b) {
+    const uint32_t m = __ballot_sync(FULL_MASK, (d >> b) & 1u);
+    peers &= ((d >> b) & 1u) ? m : ~m;
+  }
+  return peers;
+}
+
+// One LSD pass over a 4096-key tile:
+//  1. load 16 keys per thread (coalesced) and count digits per warp;
+//  2. publish the tile's digit counts to the look-back words at once, so
+//     later tiles need not wait for this tile's ranking;
+//  3. rank keys stably within each warp (ballot-built peer masks; the
+//     lowest peer bumps the warp's digit counter and shares the old value
+//     by shuffle) and place them in shared memory in digit order;
+//  4. look back for the tile's global digit offsets;
+//  5. write runs of equal digits to their global positions.
+__global__ __launch_bounds__(SORT_THREADS) void k_sort_pass(PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PassSmem& sm = *reinterpret_cast<PassSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(a.tile_ctr, 1u);
-  for (int i = tid; i < SORT_WARPS * (RADIX + 1); i += SORT_THREADS) (&s_whist[0][0])[i] = 0;
+  if (tid == 0) sm.tile = atomicAdd(a.tile_ctr, 1u);
+  for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&sm.whist[0][0])[i] = 0;
   __syncthreads();
-  const int64_t tile = s_tile;
+  const int64_t tile = sm.tile;
   const int64_t tbase = tile * SORT_TILE;
 
-  // Load: item i of lane l in warp w is tile key w*512 + i*32 + l (coalesced).
+  // 1. load (item i of lane l in warp w is tile key w*512 + i*32 + l) and count
   uint64_t k[SORT_ITEMS];
-  uint32_t dr[SORT_ITEMS];  // digit in bits 0..15, warp-local rank in bits 16..31
 #pragma unroll
   for (int i = 0; i < SORT_ITEMS; ++i) {
     const int64_t idx = tbase + warp * (32 * SORT_ITEMS) + i * 32 + lane;
-    const bool valid = idx < a.n;
-    k[i] = valid ? __ldcs(a.in + idx) : 0ULL;
-    dr[i] = valid ? (uint32_t)((k[i] >> a.shift) & (RADIX - 1)) : (uint32_t)RADIX;
+    k[i] = idx < a.n ? __ldcs(a.in + idx) : ~0ULL;
   }
-  // Warp-level multisplit rank, in item-major then lane order (stable).
-  const uint32_t lt = lanemask_lt();
-#pragma unroll
-  for (int i = 0; i < SORT_ITEMS; ++i) {
-    const uint32_t d = dr[i];
-    const uint32_t peers = __match_any_sync(FULL_MASK, d);
-    const uint32_t before = s_whist[warp][d];
-    const uint32_t r = before + __popc(peers & lt);
-    __syncwarp();
-    if ((peers & lt) == 0) s_whist[warp][d] = before + __popc(peers);
-    __syncwarp();
-    dr[i] = d | (r << 16);
-  }
-  __syncthreads();
-
-  // Thread d owns digit d: exclusive prefix over warps, tile count, block scan.
-  const int d = tid;
-  uint32_t cnt = 0;
-#pragma unroll
-  for (int w = 0; w < SORT_WARPS; ++w) {
-    const uint32_t c = s_whist[w][d];
-    s_whist[w][d] = cnt;
-    cnt += c;
-  }
-  uint32_t incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) s_wsum[warp] = incl;
-  __syncthreads();
-  uint32_t wpre = 0;
-#pragma unroll
-  for (int w = 0; w < SORT_WARPS; ++w)
-    if (w < warp) wpre += s_wsum[w];
-  const uint32_t dstart = wpre + incl - cnt;
-  s_dstart[d] = dstart;
-
-  // Decoupled look-back for this digit across tiles.
-  uint64_t* st = a.status + tile * RADIX + d;
-  uint64_t excl;
-  if (tile == 0) {
-    excl = a.base[d];
-    st_relaxed(st, lb_pack(a.epoch, LB_INC, excl + cnt));
-  } else {
-    st_relaxed(st, lb_pack(a.epoch, LB_AGG, cnt));
-    excl = lookback(a.status + d, tile, RADIX, a.epoch, a.err);
-    st_relaxed(st, lb_pack(a.epoch, LB_INC, excl + cnt));
-  }
-  s_goff[d] = excl - (uint64_t)dstart;  // global index = s_goff[d] + local position (mod 2^64)
-  __syncthreads();
-
-  // Scatter into shared memory in digit order, then out in runs.
-#pragma unroll
-  for (int i = 0; i < SORT_ITEMS; ++i) {
-    const uint32_t dd = dr[i] & 0xffffu;
-    if (dd < (uint32_t)RADIX) s_keys[s_dstart[dd] + s_whist[warp][dd] + (dr[i] >> 16)] = k[i];
-  }
-  __syncthreads();
   const int64_t left = a.n - tbase;
   const int nvalid = left < SORT_TILE ? (int)left : SORT_TILE;
 #pragma unroll
   for (int i = 0; i < SORT_ITEMS; ++i) {
+    const int li = warp * (32 * SORT_ITEMS) + i * 32 + lane;
+    if (li < nvalid) atomicAdd(&sm.whist[warp][(uint32_t)(k[i] >> a.shift) & (RADIX - 1)], 1u);
+  }
+  __syncthreads();
+
+  // 2. digit owners: warp bases, tile count, publish, block scan
+  uint32_t cnt = 0;
+  if (tid < RADIX) {
+#pragma unroll
+    for (int w = 0; w < SORT_WARPS; ++w) {
+      const uint32_t c = sm.whist[w][tid];
+      sm.whist[w][tid] = cnt;
+      cnt += c;
+    }
+    uint64_t* st = a.status + tile * RADIX + tid;
+    if (tile == 0) st_relaxed(st, lb_pack(a.epoch, LB_INC, a.base[tid] + cnt));
+    else st_relaxed(st, lb_pack(a.epoch, LB_AGG, cnt));
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) sm.wsum[warp] = incl;
+    cnt = incl - cnt;  // exclusive within the warp for now
+  }
+  __syncthreads();
+  if (tid < RADIX) {
+    uint32_t pre = 0;
+#pragma unroll
+    for (int w = 0; w < RADIX / 32; ++w)
+      if (w < warp) pre += sm.wsum[w];
+    sm.dstart[tid] = pre + cnt;
+  }
+  __syncthreads();
+
+  // 3. stable warp-level rank, scattered into shared memory in digit order
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < SORT_ITEMS; ++i) {
+    const int li = warp * (32 * SORT_ITEMS) + i * 32 + lane;
+    const uint32_t d = li < nvalid ? ((uint32_t)(k[i] >> a.shift) & (RADIX - 1)) : (uint32_t)RADIX;
+    const uint32_t peers = digit_peers(d);
+    const int leader = __ffs(peers) - 1;
+    uint32_t before = 0;
+    if (lane == leader && d < (uint32_t)RADIX) {
+      before = sm.whist[warp][d];
+      sm.whist[warp][d] = before + __popc(peers);
+    }
+    before = __shfl_sync(FULL_MASK, before, leader);
+    if (d < (uint32_t)RADIX) sm.keys[sm.dstart[d] + before + __popc(peers & lt)] = k[i];
+    __syncwarp();
+  }
+
+  // 4. look-back for the global offset of each digit
+  __syncthreads();
+  if (tid < RADIX) {
+    uint64_t excl;
+    if (tile == 0) {
+      excl = a.base[tid];
+    } else {
+      excl = lookback(a.status + tid, tile, RADIX, a.epoch, a.err);
+    }
+    // the tile count is the distance to the next digit's start
+    const uint32_t next = tid + 1 < RADIX ? sm.dstart[tid + 1] : (uint32_t)nvalid;
+    const uint32_t tc = next - sm.dstart[tid];
+    if (tile != 0) st_relaxed(a.status + tile * RADIX + tid, lb_pack(a.epoch, LB_INC, excl + tc));
+    sm.goff[tid] = excl - (uint64_t)sm.dstart[tid];
+  }
+  __syncthreads();
+
+  // 5. write out in runs
+#pragma unroll
+  for (int i = 0; i < SORT_ITEMS; ++i) {
     const int pos = i * SORT_THREADS + tid;
     if (pos < nvalid) {
-      const uint64_t key = s_keys[pos];
-      const uint32_t dd = (uint32_t)((key >> a.shift) & (RADIX - 1));
-      __stcs(a.out + (s_goff[dd] + (uint64_t)pos), key);
+      const uint64_t key = sm.keys[pos];
+      const uint32_t dd = (uint32_t)(key >> a.shift) & (RADIX - 1);
+      __stcs(a.out + (sm.goff[dd] + (uint64_t)pos), key);
     }
   }
 }
@@ -194,12 +243,19 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
   uint64_t* status = reinterpret_cast<uint64_t*>(base_ptr + 2 * MAX_PASSES * RADIX * sizeof(uint64_t) + 256);
   WEDGE_CUDA_TRY(cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, bits), s), "radix sort: clear scratch");
 
-  const int hist_blocks = sm_count() * 4;
-  wedge_status st = launch("sort_histogram", s, [&] { k_sort_hist<<<hist_blocks, 256, 0, s>>>(keys, n, passes, hist); });
+  const int hist_blocks = sm_count() * 8;
+  wedge_status st =
+      launch("sort_histogram", s, [&] { k_sort_hist<<<hist_blocks, HIST_THREADS, 0, s>>>(keys, n, passes, hist); });
   if (st != WEDGE_OK) return st;
   st = launch("sort_digit_base", s, [&] { k_sort_base<<<passes, RADIX, 0, s>>>(hist, digit_base); });
   if (st != WEDGE_OK) return st;
 
+  static bool attr_set = false;
+  if (!attr_set) {
+    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PASS_SMEM),
+                   "radix sort: shared memory");
+    attr_set = true;
+  }
   uint64_t* src = keys;
   uint64_t* dst = alt;
   for (int p = 0; p < passes; ++p) {
@@ -213,7 +269,8 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
     a.status = status;
     a.tile_ctr = ctr + p;
     a.err = derr;
-    st = launch("sort_onesweep_pass", s, [&] { k_sort_pass<<<(unsigned)tiles, SORT_THREADS, 0, s>>>(a); });
+    st = launch("sort_onesweep_pass", s,
+                [&] { k_sort_pass<<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a); });
     if (st != WEDGE_OK) return st;
     uint64_t* t = src;
     src = dst;

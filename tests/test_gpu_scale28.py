@@ -1,0 +1,124 @@
+"""Full-size check at Kronecker scale 28 (268,435,456 vertices, 4,294,967,296
+generated edges), in the configuration bench.py times.
+
+The oracle cannot build this graph in test time, so the check uses
+(a) properties that hold at any size (offsets, degrees, bins, tallies), and
+(b) outputs the oracle computes one by one: the exact neighbour sets of ~900
+vertices, recomputed from one scan of all generated edges, compared with the
+GPU rows; and for sampled global-stream wedges, the endpoints implied by the
+Philox words and the exact rows, their degrees and their closure.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+wedge = pytest.importorskip("paper_1301_5887_gb300")
+
+SCALE = 28
+K = 950114
+SEED = 7
+N_CHECK = 300
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    wedge.load()
+
+
+def _mulhi(a, b):
+    return (int(a) * int(b)) >> 64
+
+
+def test_scale28_full_size():
+    n = 1 << SCALE
+    m = graphgen.kronecker_edges(SCALE)
+    props = torch.cuda.get_device_properties(0)
+    if props.total_memory < 250 * 2**30:
+        pytest.skip("needs a GPU with >= 250 GiB")
+    src = torch.empty(m, dtype=torch.int32, device="cuda")
+    dst = torch.empty(m, dtype=torch.int32, device="cuda")
+    graphgen.kronecker_device(SCALE, src.data_ptr(), dst.data_ptr(), m, torch.cuda.current_stream().cuda_stream)
+    g = wedge.graph_build(src, dst, n)
+    del src, dst
+    torch.cuda.empty_cache()
+    wedge.trim()
+    gi = g.info()
+
+    # (a) properties of the CSR
+    off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    deg = torch.empty(n, dtype=torch.int32, device="cuda")
+    g.copy(off=off, deg=deg)
+    assert int(off[0]) == 0 and int(off[-1]) == gi.n_adj and gi.n_adj % 2 == 0
+    assert torch.equal(off[1:] - off[:-1], deg.to(torch.int64))
+    assert int(deg.max()) == gi.max_degree
+    degl = deg.to(torch.int64)
+
+    # (a) properties of the bins (tau = 1, omega = 2: bin id = bit length of d)
+    b = wedge.bin(g, tau=1, omega=2)
+    bi = b.info()
+    blen = torch.zeros_like(degl)
+    for k in range(32):  # bit length of d, in exact integer steps
+        blen += (degl >= (1 << k)).to(torch.int64)
+    n_b = torch.bincount(blen, minlength=bi.n_bins).cpu().numpy()
+    wedges = degl * (degl - 1) // 2
+    p_b = torch.zeros(bi.n_bins, dtype=torch.int64, device="cuda").index_add_(0, blen, wedges).cpu().numpy()
+    assert [int(x) for x in bi.n_b[1:bi.n_bins]] == [int(x) for x in n_b[1:bi.n_bins]]
+    assert [int(x) for x in bi.p_b[:bi.n_bins]] == [int(x) for x in p_b]
+    assert bi.p_total == int(wedges.sum())
+    assert bi.n_wedge_vertices == int((degl >= 2).sum())
+
+    # sampling in the bench configuration, with global-stream records
+    rec = torch.zeros((K, 8), dtype=torch.int32, device="cuda")
+    c = wedge.sample(g, b, seed=SEED, k_per_bin=K, k_global=K, records=rec)
+    for k in range(bi.n_bins):
+        if bi.p_b[k] > 0:
+            assert int(c.k_b[k]) == K and int(c.q[k].sum()) == K
+        else:
+            assert int(c.k_b[k]) == 0
+    assert c.k_global == K and c.closed_global == int(rec[:, 3].sum())
+    assert int(c.stats.sum()) == c.closed_global
+    recs = rec[:N_CHECK].cpu().numpy()
+
+    # (b) exact rows from one scan of the generated edges
+    rng = np.random.default_rng(0)
+    hub = int(torch.argmax(deg))
+    query = set(rng.integers(0, n, 200).tolist()) | {hub}
+    query |= set(recs[:, 0].tolist()) | set(recs[:, 1].tolist()) | set(recs[:, 2].tolist())
+    query = np.array(sorted(query), np.int32)
+    rows = oracle.rows_kronecker(SCALE, m, graphgen.RMAT_A, graphgen.RMAT_B, graphgen.RMAT_C, 1, True, query)
+    adj_ptr = gi.adj
+    q_t = torch.as_tensor(query.astype(np.int64)).cuda()
+    starts = off[q_t].cpu().numpy()
+    ends = off[q_t + 1].cpu().numpy()
+    adj = torch.empty(int(gi.n_adj), dtype=torch.int32, device="cuda")
+    g.copy(adj=adj)
+    for v, a, z in zip(query.tolist(), starts.tolist(), ends.tolist()):
+        got = adj[a:z].cpu().numpy()
+        assert np.array_equal(got, rows[v]), v
+    del adj
+    assert adj_ptr != 0
+
+    # (b) sampled global wedges: endpoints from the Philox words and exact rows
+    L, W = b.arrays_numpy()
+    for s, (v0, v1, v2, closed, d0, d1, d2, _) in enumerate(recs.tolist()):
+        row0 = rows[v0]
+        assert d0 == row0.shape[0] and d1 == rows[v1].shape[0] and d2 == rows[v2].shape[0]
+        r = oracle.philox4x32_10([s & 0xFFFFFFFF, s >> 32, 0, 1], [SEED & 0xFFFFFFFF, SEED >> 32])
+        t = _mulhi(int(r[0]) | (int(r[1]) << 32), bi.p_total)
+        kb = int(d0).bit_length()  # L is ordered by (bin, id)
+        lo, hi = bi.start[kb], bi.start[kb + 1]
+        j = lo + int(np.searchsorted(L[lo:hi], v0))
+        assert int(L[j]) == v0
+        assert int(W[j]) <= t < int(W[j + 1])
+        u = _mulhi(int(r[2]) | (int(r[3]) << 32), d0 * (d0 - 1))
+        i, jp = divmod(u, d0 - 1)
+        jj = jp + (1 if jp >= i else 0)
+        assert v1 == int(row0[i]) and v2 == int(row0[jj])
+        assert bool(closed) == bool(np.isin(v2, rows[v1]))
