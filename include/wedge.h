@@ -66,7 +66,7 @@ WEDGE_API const char* wedge_last_error(void);
 WEDGE_API uint32_t wedge_version(void);
 /* sizeof of the ABI structs, for bindings to check their layouts: fills up to
  * cap of [graph_info, bins_info, sample_params, record, counts, estimates,
- * kernel_stat] and returns 7. */
+ * kernel_stat, request, launch_config] and returns 9. */
 WEDGE_API int wedge_abi_sizes(uint64_t* sizes, int cap);
 
 /* --------------------------------------------------------------------------
@@ -168,6 +168,9 @@ WEDGE_API wedge_status wedge_bins_copy(const wedge_bins* b, int32_t* L, uint64_t
  * depend only on (graph, bins, seed, budgets), never on launch shape.
  *
  * Budgets: k_per_bin (k_global) = 0 means ceil(0.5 eps^-2 ln(2/delta)) (Thm 3.1).
+ * k_bin: optional host array of n_bins per-bin budgets indexed by bin id
+ * (k_bin[b] samples for bin b; 0 skips the bin); when set it replaces
+ * k_per_bin.
  * records: optional device buffer of k_global wedge_record entries, written
  * for the global stream in sample order (NULL: none).
  * Errors: EINVAL if eps or delta is outside (0,1) while a budget is 0,
@@ -184,7 +187,8 @@ typedef struct {
   uint64_t k_per_bin;
   uint64_t k_global;
   uint32_t flags;
-  void* records; /* device wedge_record[k_global] or NULL */
+  void* records;        /* device wedge_record[k_global] or NULL */
+  const uint64_t* k_bin; /* host uint64[n_bins] per-bin budgets or NULL */
 } wedge_sample_params;
 
 typedef struct {
@@ -209,6 +213,67 @@ typedef struct {
 /* Host `out` is filled after the stream is synchronised. */
 WEDGE_API wedge_status wedge_sample(const wedge_graph* g, const wedge_bins* b, const wedge_sample_params* sp, wedge_stream s,
                           wedge_counts* out);
+
+/* --------------------------------------------------------------------------
+ * Batched sampling: many requests in one persistent launch.
+ *
+ * A request is one wedge_sample call (graph, its bins, parameters). All
+ * requests' streams are cut into tiles of consecutive sample indices;
+ * persistent CTAs (one resident wave) pop tiles from an atomic ticket until
+ * the list is exhausted. Each request's counts are bit-identical to
+ * wedge_sample with the same parameters (same Philox counters), for any mix,
+ * order, tile size or mapping. The paper runs one job per graph; this is the
+ * GPU counterpart of serving many graphs and budgets at once.
+ *
+ * Launch configuration: a tile is drawn one sample per thread
+ * (WEDGE_MAP_THREAD: binary searches) or one sample per warp
+ * (WEDGE_MAP_WARP: 33-way cooperative searches of W and of the closure row),
+ * chosen per stream class by the number of vertices the stream searches
+ * (small < 2^12, medium < 2^20, large). block_threads is 128, 256 or 512
+ * (0 = 256); samples_per_tile defaults to 2048. wedge_autotune times
+ * candidate configurations on the requests (budgets scaled down 8x) and
+ * returns the fastest; results are cached per device and request-shape
+ * signature in memory and, if the environment variable WEDGE_TUNE_CACHE
+ * names a file, in that file.
+ *
+ * wedge_batch_create builds the work list on the device (synchronising s)
+ * and captures clear + kernel + copy-back into a CUDA graph;
+ * wedge_batch_launch replays it on s (reusable; asynchronous);
+ * wedge_batch_results waits for the last launch and fills out[n_reqs].
+ * The graphs and bins must outlive the batch. Errors: EINVAL for NULL
+ * handles, bins of another graph, a 0 budget with eps/delta outside (0,1),
+ * or a bad configuration; ENOMEM; ECUDA.
+ * ------------------------------------------------------------------------ */
+#define WEDGE_MAP_THREAD 1u
+#define WEDGE_MAP_WARP 2u
+
+typedef struct {
+  const wedge_graph* graph;
+  const wedge_bins* bins;
+  wedge_sample_params params;
+} wedge_request;
+
+typedef struct {
+  uint32_t mapping_small;    /* streams over < 2^12 vertices (0 = thread) */
+  uint32_t mapping_medium;   /* streams over < 2^20 vertices */
+  uint32_t mapping_large;
+  uint32_t block_threads;    /* 128, 256 or 512 (0 = 256) */
+  uint32_t samples_per_tile; /* 0 = 2048 */
+} wedge_launch_config;
+
+typedef struct wedge_batch wedge_batch;
+
+WEDGE_API wedge_status wedge_batch_create(const wedge_request* reqs, int n_reqs, const wedge_launch_config* cfg,
+                                          wedge_stream s, wedge_batch** out);
+WEDGE_API wedge_status wedge_batch_launch(wedge_batch* b, wedge_stream s);
+WEDGE_API wedge_status wedge_batch_results(wedge_batch* b, wedge_counts* out);
+WEDGE_API void wedge_batch_free(wedge_batch* b);
+/* Sizes of a planned batch: streams, tiles, persistent grid (any may be NULL). */
+WEDGE_API wedge_status wedge_batch_info(const wedge_batch* b, uint32_t* n_streams, uint32_t* n_tiles, uint32_t* grid);
+/* create + launch + results + free. */
+WEDGE_API wedge_status wedge_sample_batch(const wedge_request* reqs, int n_reqs, const wedge_launch_config* cfg,
+                                          wedge_stream s, wedge_counts* out);
+WEDGE_API wedge_status wedge_autotune(const wedge_request* reqs, int n_reqs, wedge_stream s, wedge_launch_config* out);
 
 /* Smallest k with k >= 0.5 eps^-2 ln(2/delta) (Thm 3.1); 0 if eps or delta is outside (0,1). */
 WEDGE_API uint64_t wedge_hoeffding_k(double eps, double delta);

@@ -59,7 +59,7 @@ def _L():
         _lib.oracle_philox4x32_10.restype = None
         _lib.oracle_hoeffding_k.argtypes = [dbl, dbl]
         _lib.oracle_hoeffding_k.restype = u64
-        _lib.oracle_sample.argtypes = [i32, P, P, u32, u64, i32, u64, u64, u64, P, P, P, P]
+        _lib.oracle_sample.argtypes = [i32, P, P, u32, u64, i32, u64, u64, u64, P, P, P, P, P]
         _lib.oracle_sample.restype = ctypes.c_int
         _lib.oracle_classify.argtypes = [i32, P, P, u32, u64, i64, P, P, P, P]
         _lib.oracle_classify.restype = ctypes.c_int
@@ -157,10 +157,12 @@ def hoeffding_k(eps: float, delta: float) -> int:
 # Sampling, classification, exact counts
 # --------------------------------------------------------------------------
 
-def sample(off, adj, tau: int, omega: int, seed: int, k_per_bin: int, k_global: int, records: bool = False):
+def sample(off, adj, tau: int, omega: int, seed: int, k_per_bin: int, k_global: int, records: bool = False,
+           k_bins=None):
     """Per-bin and global wedge sampling (Thm 3.2, Thm 3.3, Sec. 3.2) with the
     tally of Alg. Phase 4c. Returns counts[n_bins, 5] = (k_b, q0, q1, q2, q3),
-    glob = (k_global, closed), stats[34, 34] and optional records[k_global, 8]."""
+    glob = (k_global, closed), stats[34, 34] and optional records[k_global, 8].
+    k_bins (optional, indexed by bin id) gives each bin its own budget."""
     off = _c(off, np.int64)
     adj = _c(adj, np.int32)
     n = off.shape[0] - 1
@@ -169,8 +171,14 @@ def sample(off, adj, tau: int, omega: int, seed: int, k_per_bin: int, k_global: 
     glob = np.zeros(2, np.uint64)
     stats = np.zeros((STAT_BINS, STAT_BINS), np.uint64)
     rec = np.zeros((k_global, 8), np.int32) if records else None
+    kb = None
+    if k_bins is not None:
+        kb = np.zeros(nb, np.uint64)
+        src = np.asarray(k_bins, dtype=np.uint64)
+        kb[: min(nb, src.shape[0])] = src[:nb]
     rc = _L().oracle_sample(n, _p(off), _p(adj), tau, omega, nb, seed, k_per_bin, k_global, _p(counts), _p(glob),
-                            _p(stats), _p(rec) if records else ctypes.c_void_p(0))
+                            _p(stats), _p(rec) if records else ctypes.c_void_p(0),
+                            _p(kb) if kb is not None else ctypes.c_void_p(0))
     if rc != 0:
         raise RuntimeError(f"oracle_sample failed ({rc})")
     return {"counts": counts, "glob": glob, "stats": stats, "records": rec}

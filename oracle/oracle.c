@@ -250,11 +250,12 @@ static wedge_t draw_wedge(const int64_t* off, const int32_t* adj, const int32_t*
  * counting closed ones. counts[b*5 + 0..4] = (k_b, q0, q1, q2, q3) for
  * b < n_bins; glob[0..1] = (k_global, closed); stats[34*34] = closed global
  * wedges by (BinId22(d_min), BinId22(d_max)); rec (optional, 8 int32 per
- * global sample) = (v0, v1, v2, closed, d0, d1, d2, 0).
+ * global sample) = (v0, v1, v2, closed, d0, d1, d2, 0). k_bins (optional,
+ * n_bins entries) gives each bin its own budget in place of k_per_bin.
  * Returns 0, -1 if n_bins is too small, -2 on allocation failure. */
 OR_EXPORT int oracle_sample(int32_t n, const int64_t* off, const int32_t* adj, uint32_t tau, uint64_t omega,
                             int32_t n_bins, uint64_t seed, uint64_t k_per_bin, uint64_t k_global,
-                            uint64_t* counts, uint64_t* glob, uint64_t* stats, int32_t* rec) {
+                            uint64_t* counts, uint64_t* glob, uint64_t* stats, int32_t* rec, const uint64_t* k_bins) {
   for (int32_t b = 0; b < n_bins * 5; ++b) counts[b] = 0;
   glob[0] = glob[1] = 0;
   for (int i = 0; i < OR_STAT_BINS * OR_STAT_BINS; ++i) stats[i] = 0;
@@ -300,7 +301,7 @@ OR_EXPORT int oracle_sample(int32_t n, const int64_t* off, const int32_t* adj, u
     const int64_t s0 = start[b], nb = start[b + 1] - start[b];
     if (nb == 0) continue;
     const uint64_t p = cum_bin[start[b + 1] - 1];
-    const uint64_t k = k_per_bin;
+    const uint64_t k = k_bins ? k_bins[b] : k_per_bin;
     uint64_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
 #pragma omp parallel for schedule(static) reduction(+ : q0, q1, q2, q3)
     for (int64_t s = 0; s < (int64_t)k; ++s) {

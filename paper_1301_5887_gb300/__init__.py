@@ -68,7 +68,7 @@ class BinsInfo(ctypes.Structure):
 class SampleParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("eps", ctypes.c_double), ("delta", ctypes.c_double),
                 ("k_per_bin", ctypes.c_uint64), ("k_global", ctypes.c_uint64), ("flags", ctypes.c_uint32),
-                ("records", _vp)]
+                ("records", _vp), ("k_bin", _vp)]
 
 
 class Record(ctypes.Structure):
@@ -93,14 +93,32 @@ class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
 
-_STRUCTS = [GraphInfo, BinsInfo, SampleParams, Record, CountsStruct, EstimatesStruct, KernelStat]
+class Request(ctypes.Structure):
+    _fields_ = [("graph", _vp), ("bins", _vp), ("params", SampleParams)]
+
+
+class LaunchConfig(ctypes.Structure):
+    _fields_ = [("mapping_small", ctypes.c_uint32), ("mapping_medium", ctypes.c_uint32),
+                ("mapping_large", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
+                ("samples_per_tile", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+MAP_THREAD = 1
+MAP_WARP = 2
+
+_STRUCTS = [GraphInfo, BinsInfo, SampleParams, Record, CountsStruct, EstimatesStruct, KernelStat, Request,
+            LaunchConfig]
 
 # Every symbol include/wedge.h declares.
 EXPORTS = ["wedge_status_str", "wedge_last_error", "wedge_version", "wedge_abi_sizes", "wedge_graph_build",
            "wedge_graph_free", "wedge_graph_get_info", "wedge_graph_copy", "wedge_bin", "wedge_bins_free",
            "wedge_bins_get_info", "wedge_bins_copy", "wedge_sample", "wedge_hoeffding_k", "wedge_estimate", "wedge_classify",
            "wedge_profile_enable", "wedge_profile_reset", "wedge_profile_read", "wedge_trim",
-           "wedge_degree_offsets_noalloc"]
+           "wedge_degree_offsets_noalloc", "wedge_batch_create", "wedge_batch_launch", "wedge_batch_results",
+           "wedge_batch_free", "wedge_batch_info", "wedge_sample_batch", "wedge_autotune"]
 
 _lib = None
 
@@ -142,13 +160,20 @@ def load():
         "wedge_profile_read": ([P, ctypes.c_int], ctypes.c_int),
         "wedge_trim": ([], st),
         "wedge_degree_offsets_noalloc": ([P, i64, P, P], st),
+        "wedge_batch_create": ([P, ctypes.c_int, P, P, P], st),
+        "wedge_batch_launch": ([P, P], st),
+        "wedge_batch_results": ([P, P], st),
+        "wedge_batch_free": ([P], None),
+        "wedge_batch_info": ([P, P, P, P], st),
+        "wedge_sample_batch": ([P, ctypes.c_int, P, P, P], st),
+        "wedge_autotune": ([P, ctypes.c_int, P, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = res
-    sizes = (ctypes.c_uint64 * 8)()
-    lib.wedge_abi_sizes(sizes, 8)
+    sizes = (ctypes.c_uint64 * 16)()
+    lib.wedge_abi_sizes(sizes, 16)
     for i, S in enumerate(_STRUCTS):
         if sizes[i] != ctypes.sizeof(S):
             raise ImportError(f"ABI mismatch for {S.__name__}: C {sizes[i]} bytes, binding {ctypes.sizeof(S)}")
@@ -318,10 +343,21 @@ class Counts:
         return np.concatenate([self.k_b[:, None], self.q], axis=1)
 
 
+def _budget_array(k_bin):
+    if k_bin is None:
+        return None
+    return np.ascontiguousarray(np.asarray(k_bin, dtype=np.uint64))
+
+
 def sample(graph: Graph, bins: Bins, seed: int, eps: float = 0.0, delta: float = 0.0, k_per_bin: int = 0,
-           k_global: int = 0, flags: int = 0, records=None, stream=None) -> Counts:
+           k_global: int = 0, flags: int = 0, records=None, stream=None, k_bin=None) -> Counts:
+    """k_bin: optional per-bin budgets indexed by bin id (length >= n_bins)."""
     lib = load()
-    sp = SampleParams(seed, eps, delta, k_per_bin, k_global, flags, _ptr(records)[0] if records is not None else 0)
+    kb = _budget_array(k_bin)
+    if kb is not None and kb.shape[0] < bins.info().n_bins:
+        raise ValueError("k_bin needs one entry per bin id")
+    sp = SampleParams(seed, eps, delta, k_per_bin, k_global, flags, _ptr(records)[0] if records is not None else 0,
+                      kb.ctypes.data if kb is not None else 0)
     c = CountsStruct()
     _check(lib.wedge_sample(graph.handle, bins.handle, ctypes.byref(sp), _stream_handle(stream), ctypes.byref(c)))
     return Counts(c)
@@ -383,3 +419,98 @@ def profile_read() -> dict:
 
 def trim():
     _check(load().wedge_trim())
+
+
+# ---------------------------------------------------------------------------
+# Batched sampling (wedge_batch_*, wedge_autotune)
+# ---------------------------------------------------------------------------
+
+class Requests:
+    """A C array of wedge_request plus the host budget arrays it points to."""
+
+    def __init__(self, items):
+        """items: iterable of dicts with graph, bins, seed and any of eps, delta,
+        k_per_bin, k_global, k_bin, flags, records."""
+        items = list(items)
+        self.n = len(items)
+        self.array = (Request * max(self.n, 1))()
+        self._keep = []
+        for i, it in enumerate(items):
+            kb = _budget_array(it.get("k_bin"))
+            if kb is not None:
+                self._keep.append(kb)
+            rec = it.get("records")
+            if rec is not None:
+                self._keep.append(rec)
+            self.array[i].graph = it["graph"].handle
+            self.array[i].bins = it["bins"].handle
+            self.array[i].params = SampleParams(it.get("seed", 0), it.get("eps", 0.0), it.get("delta", 0.0),
+                                                it.get("k_per_bin", 0), it.get("k_global", 0), it.get("flags", 0),
+                                                _ptr(rec)[0] if rec is not None else 0,
+                                                kb.ctypes.data if kb is not None else 0)
+        self.items = items
+
+
+def _config(cfg):
+    if cfg is None:
+        return None
+    if isinstance(cfg, LaunchConfig):
+        return cfg
+    c = LaunchConfig()
+    for k, v in cfg.items():
+        setattr(c, k, int(v))
+    return c
+
+
+class Batch:
+    """A planned batch (work list on the device, CUDA-graph-captured launch)."""
+
+    def __init__(self, requests: Requests, cfg=None, stream=None):
+        lib = load()
+        self.requests = requests
+        c = _config(cfg)
+        h = ctypes.c_void_p()
+        _check(lib.wedge_batch_create(requests.array, requests.n, ctypes.byref(c) if c is not None else None,
+                                      _stream_handle(stream), ctypes.byref(h)))
+        self._h = h.value
+
+    def info(self):
+        ns, nt, gr = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        _check(load().wedge_batch_info(self._h, ctypes.byref(ns), ctypes.byref(nt), ctypes.byref(gr)))
+        return {"streams": ns.value, "tiles": nt.value, "grid": gr.value}
+
+    def launch(self, stream=None):
+        _check(load().wedge_batch_launch(self._h, _stream_handle(stream)))
+
+    def results(self):
+        out = (CountsStruct * max(self.requests.n, 1))()
+        _check(load().wedge_batch_results(self._h, out))
+        return [Counts(out[i]) for i in range(self.requests.n)]
+
+    def free(self):
+        if self._h:
+            load().wedge_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sample_batch(requests: Requests, cfg=None, stream=None):
+    """All requests in one persistent launch (wedge_sample_batch)."""
+    lib = load()
+    c = _config(cfg)
+    out = (CountsStruct * max(requests.n, 1))()
+    _check(lib.wedge_sample_batch(requests.array, requests.n, ctypes.byref(c) if c is not None else None,
+                                  _stream_handle(stream), out))
+    return [Counts(out[i]) for i in range(requests.n)]
+
+
+def autotune(requests: Requests, stream=None) -> LaunchConfig:
+    lib = load()
+    c = LaunchConfig()
+    _check(lib.wedge_autotune(requests.array, requests.n, _stream_handle(stream), ctypes.byref(c)))
+    return c

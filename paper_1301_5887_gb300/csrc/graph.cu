@@ -5,9 +5,11 @@
 // (u << b) | v, sorted by a device radix sort, deduplicated and cut into rows:
 //   1. expand: each input pair (u, v), u != v, emits (u,v) and (v,u); self-loops
 //      emit a sentinel that sorts last; ids outside [0, n) raise DERR_BAD_ID.
+//      The sort's digit histograms are accumulated here as the keys appear.
 //   2. sort: LSD radix over the 2b significant bits.
 //   3. dedup: adjacent-unique keys become adjacency entries (low b bits);
-//      warp-aggregated atomics count each row's length (the degree).
+//      one atomic per run of equal sources per warp counts each row's
+//      length (the degree).
 //   4. offsets: exclusive scan of degrees into int64 row offsets.
 #include <algorithm>
 #include <atomic>
@@ -23,9 +25,15 @@ constexpr int DEDUP_THREADS = 256;
 constexpr int DEDUP_ITEMS = 16;
 constexpr int DEDUP_TILE = DEDUP_THREADS * DEDUP_ITEMS;
 
+// Expand edges to packed keys and accumulate the radix sort's digit
+// histograms (8-bit digits, `passes` of them) in shared memory on the way.
 __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                                                int64_t m, int32_t n, uint32_t b, uint64_t sentinel,
-                                                ulonglong2* __restrict__ keys, uint32_t* err) {
+                                                int64_t m, int32_t n, uint32_t b, uint64_t sentinel, int passes,
+                                                ulonglong2* __restrict__ keys, unsigned long long* __restrict__ hist,
+                                                uint32_t* err) {
+  __shared__ uint32_t sh[SORT_MAX_PASSES * 256];
+  for (int i = threadIdx.x; i < SORT_MAX_PASSES * 256; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
     const int32_t u = __ldcs(src + e), v = __ldcs(dst + e);
@@ -40,12 +48,19 @@ __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src,
       kv.y = ((uint64_t)v << b) | (uint64_t)u;
     }
     __stcs(keys + e, kv);
+    for (int p = 0; p < passes; ++p) {
+      atomicAdd(&sh[p * 256 + (uint32_t)((kv.x >> (8 * p)) & 255u)], 1u);
+      atomicAdd(&sh[p * 256 + (uint32_t)((kv.y >> (8 * p)) & 255u)], 1u);
+    }
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], (unsigned long long)sh[i]);
 }
 
 // Adjacent-unique of sorted keys -> adjacency entries and row lengths.
 __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restrict__ keys, int64_t nkeys, uint32_t b,
-                                                         uint64_t sentinel, int32_t* __restrict__ adj,
+                                                         int32_t n, uint64_t sentinel, int32_t* __restrict__ adj,
                                                          int32_t* __restrict__ deg, uint64_t* status,
                                                          uint32_t* tile_ctr, uint32_t* err, int64_t* n_unique) {
   __shared__ uint32_t s_tile;
@@ -63,10 +78,15 @@ __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restr
   uint32_t wcount = 0;
   uint64_t prev_last = ~0ULL;  // key just before this warp's first item
   if (lane == 0 && wbase > 0 && wbase - 1 < nkeys) prev_last = keys[wbase - 1];
+  // all loads first, so their latencies overlap
 #pragma unroll
   for (int i = 0; i < DEDUP_ITEMS; ++i) {
     const int64_t idx = wbase + i * 32 + lane;
     k[i] = idx < nkeys ? __ldcs(keys + idx) : sentinel;
+  }
+#pragma unroll
+  for (int i = 0; i < DEDUP_ITEMS; ++i) {
+    const int64_t idx = wbase + i * 32 + lane;
     const uint64_t up = __shfl_up_sync(FULL_MASK, k[i], 1);
     const uint64_t from31 = __shfl_sync(FULL_MASK, k[i > 0 ? i - 1 : 0], 31);
     const uint64_t prev = lane > 0 ? up : (i > 0 ? from31 : prev_last);
@@ -95,13 +115,23 @@ __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restr
   uint64_t pos = s_excl;
   for (int w = 0; w < warp; ++w) pos += s_wcount[w];
   const uint32_t lt = lanemask_lt();
+  const uint32_t le = lt | (1u << lane);
 #pragma unroll
   for (int i = 0; i < DEDUP_ITEMS; ++i) {
     const bool f = (bal[i] >> lane) & 1u;
-    const uint32_t u = f ? (uint32_t)(k[i] >> b) : 0xffffffffu;
     if (f) adj[pos + __popc(bal[i] & lt)] = (int32_t)(k[i] & vmask);
-    const uint32_t peers = __match_any_sync(FULL_MASK, u);
-    if (f && (peers >> lane) == 1u) atomicAdd(deg + u, (int32_t)__popc(peers));  // highest lane of the run
+    // Row lengths: sorted keys put equal sources in consecutive lanes. The
+    // last lane of each run adds the run's unique keys to its row's degree.
+    const uint32_t u = (uint32_t)(k[i] >> b);
+    const uint32_t u_prev = __shfl_up_sync(FULL_MASK, u, 1);
+    const uint32_t u_next = __shfl_down_sync(FULL_MASK, u, 1);
+    const uint32_t starts = __ballot_sync(FULL_MASK, lane == 0 || u_prev != u);
+    const bool run_end = lane == 31 || u_next != u;
+    if (run_end && u < (uint32_t)n) {
+      const int start = 31 - __clz(starts & le);
+      const uint32_t c = __popc(bal[i] & le & ~((1u << start) - 1u));
+      if (c) atomicAdd(deg + u, (int32_t)c);
+    }
     pos += __popc(bal[i]);
   }
 }
@@ -220,9 +250,12 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
                  std::max(scan_scratch_bytes(nkeys), scan_scratch_bytes(n_vertices)));
     if ((st = dalloc(&bb.scratch, scratch_bytes, s, "wedge_graph_build: scratch")) != WEDGE_OK) return bail(st);
 
+    const int passes = (2 * (int)b + 7) / 8;
+    if ((st = sort_clear_hist(bb.scratch, s)) != WEDGE_OK) return bail(st);
     st = launch("expand_edges", s, [&] {
-      k_expand<<<grid_stride_blocks(n_edges, 256), 256, 0, s>>>(s_in, d_in, n_edges, n_vertices, b, sentinel,
-                                                                reinterpret_cast<ulonglong2*>(bb.keys_a), bb.derr);
+      k_expand<<<grid_stride_blocks(n_edges, 256), 256, 0, s>>>(s_in, d_in, n_edges, n_vertices, b, sentinel, passes,
+                                                                reinterpret_cast<ulonglong2*>(bb.keys_a),
+                                                                sort_hist_area(bb.scratch), bb.derr);
     });
     if (st != WEDGE_OK) return bail(st);
     // Staging buffers are no longer needed once the keys exist.
@@ -231,7 +264,7 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     bb.src_dev = bb.dst_dev = nullptr;
 
     uint64_t* sorted = nullptr;
-    st = radix_sort_u64(bb.keys_a, bb.keys_b, nkeys, 2 * (int)b, bb.scratch, bb.derr, s, &sorted);
+    st = radix_sort_u64(bb.keys_a, bb.keys_b, nkeys, 2 * (int)b, bb.scratch, bb.derr, s, &sorted, true);
     if (st != WEDGE_OK) return bail(st);
 
     const int64_t tiles = (nkeys + DEDUP_TILE - 1) / DEDUP_TILE;
@@ -239,7 +272,7 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     uint32_t* ctr = static_cast<uint32_t*>(bb.scratch);
     uint64_t* status = reinterpret_cast<uint64_t*>(static_cast<char*>(bb.scratch) + 256);
     st = launch("dedup_rows", s, [&] {
-      k_dedup<<<(unsigned)tiles, DEDUP_THREADS, 0, s>>>(sorted, nkeys, b, sentinel, g->adj, g->deg, status, ctr,
+      k_dedup<<<(unsigned)tiles, DEDUP_THREADS, 0, s>>>(sorted, nkeys, b, n_vertices, sentinel, g->adj, g->deg, status, ctr,
                                                         bb.derr, bb.scalars);
     });
     if (st != WEDGE_OK) return bail(st);

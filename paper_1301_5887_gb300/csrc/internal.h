@@ -31,10 +31,16 @@ struct wedge_bins {
 
 namespace wedge {
 
-// Sort-scratch size and sort (sort.cu).
+// Sort-scratch size and sort (sort.cu). The scratch starts with the digit
+// histograms (8 passes x 256 unsigned long long); a caller that produces the
+// keys may accumulate them there itself (sort_clear_hist first) and pass
+// hist_ready = true.
+constexpr int SORT_MAX_PASSES = 8;
 size_t sort_scratch_bytes(int64_t n, int bits);
+unsigned long long* sort_hist_area(void* scratch);
+wedge_status sort_clear_hist(void* scratch, cudaStream_t s);
 wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, void* scratch, uint32_t* derr,
-                            cudaStream_t s, uint64_t** sorted);
+                            cudaStream_t s, uint64_t** sorted, bool hist_ready);
 
 // Exclusive scans with decoupled look-back (scan.cu).
 size_t scan_scratch_bytes(int64_t n);

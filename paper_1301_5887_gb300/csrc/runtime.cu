@@ -179,11 +179,11 @@ const char* wedge_last_error(void) { return g_err; }
 uint32_t wedge_version(void) { return 0x000100u; }
 
 int wedge_abi_sizes(uint64_t* sizes, int cap) {
-  const uint64_t v[7] = {sizeof(wedge_graph_info), sizeof(wedge_bins_info), sizeof(wedge_sample_params),
-                         sizeof(wedge_record),     sizeof(wedge_counts),    sizeof(wedge_estimates),
-                         sizeof(wedge_kernel_stat)};
-  for (int i = 0; i < 7 && i < cap && sizes; ++i) sizes[i] = v[i];
-  return 7;
+  const uint64_t v[9] = {sizeof(wedge_graph_info), sizeof(wedge_bins_info),  sizeof(wedge_sample_params),
+                         sizeof(wedge_record),     sizeof(wedge_counts),     sizeof(wedge_estimates),
+                         sizeof(wedge_kernel_stat), sizeof(wedge_request),   sizeof(wedge_launch_config)};
+  for (int i = 0; i < 9 && i < cap && sizes; ++i) sizes[i] = v[i];
+  return 9;
 }
 
 const char* wedge_status_str(wedge_status st) {

@@ -19,6 +19,7 @@
 #include "device.cuh"
 #include "internal.h"
 #include "runtime.h"
+#include "sample_device.cuh"
 
 namespace wedge {
 namespace {
@@ -54,27 +55,6 @@ struct SampleArgs {
   wedge_record* records;       // global stream records or nullptr
 };
 
-// Is x in the ascending row adj[lo, hi)?
-__device__ __forceinline__ bool row_contains(const int32_t* __restrict__ adj, int64_t lo, int64_t hi, int32_t x) {
-  while (hi - lo > 8) {
-    const int64_t mid = lo + ((hi - lo) >> 1);
-    if (__ldg(adj + mid) <= x) lo = mid; else hi = mid;
-  }
-  for (int64_t i = lo; i < hi; ++i) {
-    const int32_t y = __ldg(adj + i);
-    if (y == x) return true;
-    if (y > x) return false;
-  }
-  return false;
-}
-
-// Closure of the wedge (v1, v0, v2): search in the smaller (degree, id) endpoint's row.
-__device__ __forceinline__ bool closed_wedge(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-                                             int32_t v1, int32_t v2, int64_t o1, int64_t d1, int64_t o2, int64_t d2) {
-  if (d1 < d2 || (d1 == d2 && v1 < v2)) return row_contains(adj, o1, o1 + d1, v2);
-  return row_contains(adj, o2, o2 + d2, v1);
-}
-
 __global__ __launch_bounds__(SAMPLE_THREADS) void k_sample(SampleArgs a) {
   __shared__ StreamDesc s_desc;
   __shared__ int s_stream;
@@ -96,6 +76,7 @@ __global__ __launch_bounds__(SAMPLE_THREADS) void k_sample(SampleArgs a) {
   __syncthreads();
   const StreamDesc desc = s_desc;
   const BinTable bt{s_lo, a.nb, a.pow2};
+  const GraphView gv{a.off, a.adj, a.L, a.W};
   const bool global = desc.tag != 0;
   const uint64_t first = ((uint64_t)blockIdx.x - desc.tile_begin) * SAMPLE_TILE;
   uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
@@ -103,28 +84,10 @@ __global__ __launch_bounds__(SAMPLE_THREADS) void k_sample(SampleArgs a) {
     const uint64_t s = first + (uint64_t)j * SAMPLE_THREADS + tid;
     if (s >= desc.k) break;
     const Philox4 r = philox4x32_10((uint32_t)s, (uint32_t)(s >> 32), desc.bin, desc.tag, a.seed_lo, a.seed_hi);
-    // Centre: inverse CDF over the stream's wedge prefix.
-    const uint64_t t = mulhi64((uint64_t)r.r0 | ((uint64_t)r.r1 << 32), desc.p);
-    const uint64_t T = desc.wbase + t;
-    int64_t lo = desc.start, hi = desc.start + desc.len;  // W[lo] <= T < W[hi]
-    while (hi - lo > 1) {
-      const int64_t mid = lo + ((hi - lo) >> 1);
-      if (__ldg(a.W + mid) <= T) lo = mid; else hi = mid;
-    }
-    const int32_t v0 = __ldg(a.L + lo);
-    const int64_t o0 = __ldg(a.off + v0);
-    const int64_t d0 = __ldg(a.off + v0 + 1) - o0;
-    // Two distinct neighbours: an ordered pair (i, j), i != j, uniform over d(d-1).
-    const uint64_t dm1 = (uint64_t)(d0 - 1);
-    const uint64_t u = mulhi64((uint64_t)r.r2 | ((uint64_t)r.r3 << 32), (uint64_t)d0 * dm1);
-    const uint64_t i = u / dm1;
-    const uint64_t jp = u - i * dm1;
-    const uint64_t jj = jp + (jp >= i ? 1ULL : 0ULL);
-    const int32_t v1 = __ldg(a.adj + o0 + (int64_t)i);
-    const int32_t v2 = __ldg(a.adj + o0 + (int64_t)jj);
-    const int64_t o1 = __ldg(a.off + v1), d1 = __ldg(a.off + v1 + 1) - o1;
-    const int64_t o2 = __ldg(a.off + v2), d2 = __ldg(a.off + v2 + 1) - o2;
-    const bool closed = closed_wedge(a.off, a.adj, v1, v2, o1, d1, o2, d2);
+    const Wedge w = draw_wedge_thread(gv, desc.start, desc.len, desc.p, desc.wbase, r);
+    const int32_t v0 = w.v0, v1 = w.v1, v2 = w.v2;
+    const int64_t d0 = w.d0, d1 = w.d1, d2 = w.d2;
+    const bool closed = w.closed;
     if (!global) {
       if (!closed) {
         q0 += 1;
@@ -200,7 +163,7 @@ __global__ __launch_bounds__(256) void k_classify(const int64_t* __restrict__ of
     const int64_t o2 = off[v2], d2 = off[v2 + 1] - o2;
     const uint32_t b = bin_of(bt, (uint64_t)d0);
     uint8_t cls = 0;
-    if (closed_wedge(off, adj, v1, v2, o1, d1, o2, d2))
+    if (closed_wedge(adj, v1, v2, o1, d1, o2, d2))
       cls = (uint8_t)(1u + (bin_of(bt, (uint64_t)d1) == b) + (bin_of(bt, (uint64_t)d2) == b));
     q[w] = cls;
   }
@@ -225,10 +188,10 @@ extern "C" wedge_status wedge_sample(const wedge_graph* g, const wedge_bins* b, 
   const bool want_glob = !(sp->flags & WEDGE_FLAG_NO_GLOBAL);
   if (sp->records && !want_glob) return fail(WEDGE_EINVAL, "wedge_sample: records need the global stream");
   uint64_t k_bin = sp->k_per_bin, k_glob = sp->k_global;
-  if ((want_bins && k_bin == 0) || (want_glob && k_glob == 0)) {
+  if ((want_bins && k_bin == 0 && !sp->k_bin) || (want_glob && k_glob == 0)) {
     const uint64_t k = wedge_hoeffding_k(sp->eps, sp->delta);
     if (k == 0) return fail(WEDGE_EINVAL, "wedge_sample: eps and delta must lie in (0, 1) when a budget is 0");
-    if (k_bin == 0) k_bin = k;
+    if (k_bin == 0 && !sp->k_bin) k_bin = k;
     if (k_glob == 0) k_glob = k;
   }
   if (!want_bins) k_bin = 0;
@@ -258,7 +221,8 @@ extern "C" wedge_status wedge_sample(const wedge_graph* g, const wedge_bins* b, 
   // W[start[k]] is the sum of p_b over earlier bins.
   uint64_t wacc = 0;
   for (uint32_t k = 2; k < inf.n_bins; ++k) {
-    add(inf.start[k], inf.start[k + 1] - inf.start[k], inf.p_b[k], k_bin, k, 0u, wacc);
+    const uint64_t kb = !want_bins ? 0 : (sp->k_bin ? sp->k_bin[k] : k_bin);
+    add(inf.start[k], inf.start[k + 1] - inf.start[k], inf.p_b[k], kb, k, 0u, wacc);
     wacc += inf.p_b[k];
   }
   add(0, inf.n_wedge_vertices, inf.p_total, k_glob, 0u, 1u, 0ULL);

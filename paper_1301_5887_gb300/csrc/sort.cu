@@ -24,7 +24,7 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
 constexpr int SORT_ITEMS = 16;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 4096 keys
-constexpr int MAX_PASSES = 8;
+constexpr int MAX_PASSES = SORT_MAX_PASSES;
 constexpr int HIST_THREADS = 256;
 
 __global__ __launch_bounds__(HIST_THREADS) void k_sort_hist(const uint64_t* __restrict__ keys, int64_t n, int passes,
@@ -228,8 +228,15 @@ size_t sort_scratch_bytes(int64_t n, int bits) {
   return (size_t)2 * MAX_PASSES * RADIX * sizeof(uint64_t) + 256 + (size_t)tiles * RADIX * sizeof(uint64_t);
 }
 
+unsigned long long* sort_hist_area(void* scratch) { return static_cast<unsigned long long*>(scratch); }
+
+wedge_status sort_clear_hist(void* scratch, cudaStream_t s) {
+  WEDGE_CUDA_TRY(cudaMemsetAsync(scratch, 0, MAX_PASSES * RADIX * sizeof(uint64_t), s), "radix sort: clear histograms");
+  return WEDGE_OK;
+}
+
 wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, void* scratch, uint32_t* derr,
-                            cudaStream_t s, uint64_t** sorted) {
+                            cudaStream_t s, uint64_t** sorted, bool hist_ready) {
   *sorted = keys;
   if (n <= 1) return WEDGE_OK;
   const int passes = passes_for(bits);
@@ -241,12 +248,18 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
   uint64_t* digit_base = reinterpret_cast<uint64_t*>(base_ptr + MAX_PASSES * RADIX * sizeof(uint64_t));
   uint32_t* ctr = reinterpret_cast<uint32_t*>(base_ptr + 2 * MAX_PASSES * RADIX * sizeof(uint64_t));
   uint64_t* status = reinterpret_cast<uint64_t*>(base_ptr + 2 * MAX_PASSES * RADIX * sizeof(uint64_t) + 256);
-  WEDGE_CUDA_TRY(cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, bits), s), "radix sort: clear scratch");
-
-  const int hist_blocks = sm_count() * 8;
-  wedge_status st =
-      launch("sort_histogram", s, [&] { k_sort_hist<<<hist_blocks, HIST_THREADS, 0, s>>>(keys, n, passes, hist); });
-  if (st != WEDGE_OK) return st;
+  // Histograms (unless the caller already accumulated them), then the rest.
+  const size_t hist_bytes = MAX_PASSES * RADIX * sizeof(uint64_t);
+  wedge_status st = WEDGE_OK;
+  if (!hist_ready) {
+    WEDGE_CUDA_TRY(cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, bits), s), "radix sort: clear scratch");
+    const int hist_blocks = sm_count() * 8;
+    st = launch("sort_histogram", s, [&] { k_sort_hist<<<hist_blocks, HIST_THREADS, 0, s>>>(keys, n, passes, hist); });
+    if (st != WEDGE_OK) return st;
+  } else {
+    WEDGE_CUDA_TRY(cudaMemsetAsync(base_ptr + hist_bytes, 0, sort_scratch_bytes(n, bits) - hist_bytes, s),
+                   "radix sort: clear scratch");
+  }
   st = launch("sort_digit_base", s, [&] { k_sort_base<<<passes, RADIX, 0, s>>>(hist, digit_base); });
   if (st != WEDGE_OK) return st;
 

@@ -46,8 +46,10 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_struct_sizes_match(lib):
-    sizes = (ctypes.c_uint64 * 8)()
-    assert lib.wedge_abi_sizes(sizes, 8) == 7  # load() already checked each against the binding
+    sizes = (ctypes.c_uint64 * 16)()
+    n = lib.wedge_abi_sizes(sizes, 16)
+    assert n == len(wedge._STRUCTS)
+    assert [int(sizes[i]) for i in range(n)] == [ctypes.sizeof(S) for S in wedge._STRUCTS]
 
 
 def test_status_strings(lib):

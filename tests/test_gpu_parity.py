@@ -361,11 +361,12 @@ def test_profile_counts_launches():
     wedge.sample(g, b, seed=1, k_per_bin=100, k_global=100)
     st = wedge.profile_read()
     wedge.profile_enable(False)
-    for name in ["expand_edges", "sort_histogram", "sort_onesweep_pass", "dedup_rows", "scan_degrees", "bin_count",
+    for name in ["expand_edges", "sort_onesweep_pass", "dedup_rows", "scan_degrees", "bin_count",
                  "bin_scatter", "sample_closure"]:
         assert st[name]["launches"] >= 1, name
         assert st[name]["total_ms"] > 0.0, name
     assert st["sort_onesweep_pass"]["launches"] == math.ceil(2 * 10 / 8)
+    assert "sort_histogram" not in st  # digit histograms are accumulated by expand_edges
 
 
 # ---------------------------------------------------------------------------
