@@ -11,7 +11,9 @@ bins 2^i <= d < 2^(i+1), 950,114 samples per nonempty bin and globally
 Prints one JSON line. `value` is seconds per million undirected edges of the
 whole step (lower is better); `gwedges_checked_per_s` is the sampling stage
 alone. `e2e` runs the same step through the C ABI from pinned host buffers,
-host-to-device copies inside the timed region. `--impl reference` times the
+host-to-device copies inside the timed region. `batched` compares 512 plain
+single-graph sampling calls with one autotuned persistent launch over the
+same 512 requests (Kronecker and Chung-Lu graphs, per-bin budgets 1e3-1e6). `--impl reference` times the
 CPU oracle on the host cores on a bounded sample of the workload instead.
 """
 from __future__ import annotations
@@ -45,6 +47,7 @@ def parse():
     ap.add_argument("--edgefactor", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -177,6 +180,102 @@ ALG_BYTES = {
     "bin_count": lambda z: 4 * z["n"],
     "bin_scatter": lambda z: 4 * z["n"] + 12 * z["n2"],
 }
+
+
+def build_batched_mix(wedge, graphgen, torch, n_graphs=512, seed=3):
+    """The batched workload: half Kronecker graphs with scales drawn
+    log-uniformly from 8-22, half Chung-Lu power-law graphs (exponent
+    U(2.0, 2.6), mean degree U(8, 64), 2^U{10..22} vertices); per-bin and
+    global budgets drawn log-uniformly from [1e3, 1e6]."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    stream = torch.cuda.current_stream().cuda_stream
+    items, edges = [], 0
+    for i in range(n_graphs):
+        if i < n_graphs // 2:
+            scale = int(round(float(np.exp(rng.uniform(np.log(8), np.log(22))))))
+            n, m = 1 << scale, graphgen.kronecker_edges(scale)
+            s = torch.empty(m, dtype=torch.int32, device="cuda")
+            d = torch.empty(m, dtype=torch.int32, device="cuda")
+            graphgen.kronecker_device(scale, s.data_ptr(), d.data_ptr(), m, stream, seed=10_000 + i)
+            kind = f"kronecker-s{scale}"
+        else:
+            n = 1 << int(rng.integers(10, 23))
+            gamma, dbar = float(rng.uniform(2.0, 2.6)), float(rng.uniform(8, 64))
+            prefix, m = graphgen.chunglu_weights(n, gamma, dbar)
+            pd = torch.as_tensor(prefix.view(np.int64)).cuda()
+            s = torch.empty(m, dtype=torch.int32, device="cuda")
+            d = torch.empty(m, dtype=torch.int32, device="cuda")
+            graphgen.chunglu_device(pd.data_ptr(), n, s.data_ptr(), d.data_ptr(), m, 20_000 + i, stream_ptr=stream)
+            kind = f"chunglu-n{n}"
+        g = wedge.graph_build(s, d, n)
+        del s, d
+        b = wedge.bin(g, tau=TAU, omega=OMEGA)
+        nb = b.info().n_bins
+        k_bin = np.exp(rng.uniform(np.log(1e3), np.log(1e6), nb)).astype(np.uint64)
+        k_glob = int(np.exp(rng.uniform(np.log(1e3), np.log(1e6))))
+        items.append({"graph": g, "bins": b, "seed": 30_000 + i, "k_bin": k_bin, "k_global": k_glob, "kind": kind})
+        edges += m
+    return items, edges
+
+
+def bench_batched(wedge, graphgen, torch):
+    """512 plain wedge_sample calls vs one autotuned persistent launch."""
+    import numpy as np
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    items, edges = build_batched_mix(wedge, graphgen, torch)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    reqs = wedge.Requests(items)
+    t0 = time.perf_counter()
+    cfg = wedge.autotune(reqs)
+    tune_s = time.perf_counter() - t0
+
+    def plain():
+        return [wedge.sample(it["graph"], it["bins"], seed=it["seed"], k_global=it["k_global"], k_bin=it["k_bin"])
+                for it in items]
+
+    plain()  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ref = plain()
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+
+    wedge.sample_batch(reqs, cfg=cfg)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    got = wedge.sample_batch(reqs, cfg=cfg)
+    torch.cuda.synchronize()
+    batch_s = time.perf_counter() - t0
+
+    batch = wedge.Batch(reqs, cfg=cfg)
+    batch.launch()
+    batch.results()
+    t0 = time.perf_counter()
+    batch.launch()
+    got2 = batch.results()
+    replay_s = time.perf_counter() - t0
+    info = batch.info()
+    batch.free()
+
+    identical = all(np.array_equal(a.counts_matrix(), b.counts_matrix()) and a.closed_global == b.closed_global
+                    and np.array_equal(a.stats, b.stats) for a, b in zip(ref, got)) and \
+        all(np.array_equal(a.counts_matrix(), b.counts_matrix()) for a, b in zip(ref, got2))
+    samples = sum(int(c.k_b.sum()) + c.k_global for c in ref)
+    for it in items:
+        it["bins"].free()
+        it["graph"].free()
+    return {"workload": "512 graphs: 256 Kronecker (scale log-uniform 8-22) + 256 Chung-Lu (exponent 2.0-2.6, "
+                        "mean degree 8-64, 2^10-2^22 vertices); per-bin and global budgets log-uniform 1e3-1e6",
+            "graphs": len(items), "generated_edges": edges, "samples": samples,
+            "plain_calls": len(items), "plain_s": plain_s, "plain_gwedges_per_s": samples / plain_s / 1e9,
+            "batched_s": batch_s, "batched_gwedges_per_s": samples / batch_s / 1e9,
+            "replay_s": replay_s, "replay_gwedges_per_s": samples / replay_s / 1e9,
+            "speedup": plain_s / batch_s, "identical_to_plain": bool(identical),
+            "tuned_config": cfg.as_dict(), "tiles": info["tiles"], "persistent_grid": info["grid"],
+            "setup_s": setup_s, "tune_s": tune_s}
 
 
 def run_ours(args):
@@ -313,6 +412,13 @@ def run_ours(args):
                "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
         del hsrc, hdst
 
+    batched = None
+    if not args.no_batched:
+        wedge.trim()
+        torch.cuda.empty_cache()
+        batched = bench_batched(wedge, graphgen, torch)
+        wedge.trim()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, mm, ns = oracle_step(20, ef, K_SAMPLES)
@@ -331,7 +437,7 @@ def run_ours(args):
                            "bins": info["n_bins"], "samples_per_step": info["samples"],
                            "l2": f"inputs {8 * n_edges / 1e9:.1f} GB > 129 MB L2, no flush needed",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "gwedges_checked_per_s": gwps, "sampling_ms": samp_ms,
+                "gwedges_checked_per_s": gwps, "sampling_ms": samp_ms, "batched": batched,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
                 "clocks": clk, "kernels": kernels,
                 "estimates": {"c_hat": info["c_hat"], "c_hat_global": info["c_hat_global"]}}
