@@ -66,7 +66,8 @@ WEDGE_API const char* wedge_last_error(void);
 WEDGE_API uint32_t wedge_version(void);
 /* sizeof of the ABI structs, for bindings to check their layouts: fills up to
  * cap of [graph_info, bins_info, sample_params, record, counts, estimates,
- * kernel_stat, request, launch_config] and returns 9. */
+ * kernel_stat, request, launch_config, server_config, server_request,
+ * request_timing, server_metrics] and returns 13. */
 WEDGE_API int wedge_abi_sizes(uint64_t* sizes, int cap);
 
 /* --------------------------------------------------------------------------
@@ -253,12 +254,18 @@ typedef struct {
   wedge_sample_params params;
 } wedge_request;
 
+/* wedge_launch_config.flags: enqueue clear + kernel + copy-back directly on
+ * each launch instead of capturing them into a CUDA graph at create (for
+ * batches launched once). */
+#define WEDGE_BATCH_DIRECT 0x1u
+
 typedef struct {
   uint32_t mapping_small;    /* streams over < 2^12 vertices (0 = thread) */
   uint32_t mapping_medium;   /* streams over < 2^20 vertices */
   uint32_t mapping_large;
   uint32_t block_threads;    /* 128, 256 or 512 (0 = 256) */
   uint32_t samples_per_tile; /* 0 = 2048 */
+  uint32_t flags;            /* WEDGE_BATCH_DIRECT */
 } wedge_launch_config;
 
 typedef struct wedge_batch wedge_batch;
@@ -274,6 +281,87 @@ WEDGE_API wedge_status wedge_batch_info(const wedge_batch* b, uint32_t* n_stream
 WEDGE_API wedge_status wedge_sample_batch(const wedge_request* reqs, int n_reqs, const wedge_launch_config* cfg,
                                           wedge_stream s, wedge_counts* out);
 WEDGE_API wedge_status wedge_autotune(const wedge_request* reqs, int n_reqs, wedge_stream s, wedge_launch_config* out);
+
+/* --------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop over resident graphs.
+ *
+ * wedge_server_add_graph uploads an edge list (host or device), builds its
+ * CSR and bins on the server's build stream and keeps them resident. Uploads
+ * are admitted against hbm_budget_bytes: the resident footprint plus the
+ * upload's build scratch must fit; idle graphs (no queued or running
+ * request) are evicted least-recently-used first; if that is not enough
+ * the upload fails with ENOMEM and nothing is evicted that is in use.
+ * wedge_server_submit queues a sampling request on a resident graph and
+ * returns a ticket at once. A dispatcher thread keeps up to `slots` batches
+ * in flight on separate CUDA streams; whenever a slot frees up it launches
+ * every queued request (up to max_batch_requests) as one batch, so requests
+ * that arrive while others run are admitted as slots free up and overlap
+ * with them on the GPU. wedge_server_wait blocks until a ticket's request is
+ * done and returns its counts, which equal wedge_sample's for the same
+ * parameters (the mix never changes a result), and its timing. Thread-safe;
+ * destroy drains the queue and frees the resident graphs. The paper runs one
+ * MapReduce job sequence per graph; this has no counterpart there.
+ * ------------------------------------------------------------------------ */
+typedef struct wedge_server wedge_server;
+
+typedef struct {
+  uint64_t hbm_budget_bytes;   /* 0 = no limit */
+  uint32_t slots;              /* batches in flight (0 = 2, at most 16) */
+  uint32_t max_batch_requests; /* 0 = 1024 */
+  uint32_t tau;                /* binning of uploaded graphs (0 = 1) */
+  uint32_t reserved;
+  uint64_t omega;              /* (0 = 2) */
+  wedge_launch_config launch;  /* launch shape of every batch */
+} wedge_server_config;
+
+typedef struct {
+  uint64_t graph_id;
+  uint64_t seed;
+  double eps;                  /* budgets from Thm 3.1 when k_per_bin / k_global are 0 */
+  double delta;
+  uint64_t k_per_bin;
+  uint64_t k_global;
+  uint32_t flags;              /* WEDGE_FLAG_NO_GLOBAL / WEDGE_FLAG_NO_BINS */
+  uint32_t reserved;
+} wedge_server_request;
+
+typedef struct {
+  double submit_us;            /* steady-clock microseconds */
+  double dispatch_us;
+  double done_us;
+  uint32_t batch_requests;     /* requests in the batch this one ran in */
+  uint32_t reserved;
+} wedge_request_timing;
+
+typedef struct {
+  uint64_t completed;
+  uint64_t samples;
+  uint64_t batches;
+  double mean_batch_requests;
+  double p50_us;               /* submit-to-done latency, nearest rank */
+  double p99_us;
+  double mean_us;
+  double max_us;
+  double span_s;               /* first submit to last completion */
+  uint32_t resident_graphs;
+  uint32_t queued;
+  uint32_t inflight_batches;
+  uint32_t reserved;
+  uint64_t resident_bytes;
+  uint64_t evictions;
+  uint64_t rejected_uploads;
+} wedge_server_metrics;
+
+WEDGE_API wedge_status wedge_server_create(const wedge_server_config* cfg, wedge_server** out);
+WEDGE_API void wedge_server_destroy(wedge_server* sv);
+WEDGE_API wedge_status wedge_server_add_graph(wedge_server* sv, const int32_t* src, const int32_t* dst,
+                                              int64_t n_edges, int32_t n_vertices, uint64_t* graph_id);
+WEDGE_API wedge_status wedge_server_remove_graph(wedge_server* sv, uint64_t graph_id);
+WEDGE_API wedge_status wedge_server_submit(wedge_server* sv, const wedge_server_request* req, uint64_t* ticket);
+WEDGE_API wedge_status wedge_server_wait(wedge_server* sv, uint64_t ticket, wedge_counts* out,
+                                         wedge_request_timing* timing);
+/* Latency and throughput since the last reset (reset != 0 clears them after reading). */
+WEDGE_API wedge_status wedge_server_stats(wedge_server* sv, wedge_server_metrics* out, int reset);
 
 /* Smallest k with k >= 0.5 eps^-2 ln(2/delta) (Thm 3.1); 0 if eps or delta is outside (0,1). */
 WEDGE_API uint64_t wedge_hoeffding_k(double eps, double delta);

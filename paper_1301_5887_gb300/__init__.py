@@ -100,7 +100,7 @@ class Request(ctypes.Structure):
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("mapping_small", ctypes.c_uint32), ("mapping_medium", ctypes.c_uint32),
                 ("mapping_large", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
-                ("samples_per_tile", ctypes.c_uint32)]
+                ("samples_per_tile", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -108,9 +108,38 @@ class LaunchConfig(ctypes.Structure):
 
 MAP_THREAD = 1
 MAP_WARP = 2
+BATCH_DIRECT = 1
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
+                ("max_batch_requests", ctypes.c_uint32), ("tau", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("omega", ctypes.c_uint64), ("launch", LaunchConfig)]
+
+
+class ServerRequest(ctypes.Structure):
+    _fields_ = [("graph_id", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("eps", ctypes.c_double),
+                ("delta", ctypes.c_double), ("k_per_bin", ctypes.c_uint64), ("k_global", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class RequestTiming(ctypes.Structure):
+    _fields_ = [("submit_us", ctypes.c_double), ("dispatch_us", ctypes.c_double), ("done_us", ctypes.c_double),
+                ("batch_requests", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class ServerMetrics(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("samples", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("mean_batch_requests", ctypes.c_double), ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double), ("span_s", ctypes.c_double),
+                ("resident_graphs", ctypes.c_uint32), ("queued", ctypes.c_uint32),
+                ("inflight_batches", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("resident_bytes", ctypes.c_uint64), ("evictions", ctypes.c_uint64),
+                ("rejected_uploads", ctypes.c_uint64)]
+
 
 _STRUCTS = [GraphInfo, BinsInfo, SampleParams, Record, CountsStruct, EstimatesStruct, KernelStat, Request,
-            LaunchConfig]
+            LaunchConfig, ServerConfig, ServerRequest, RequestTiming, ServerMetrics]
 
 # Every symbol include/wedge.h declares.
 EXPORTS = ["wedge_status_str", "wedge_last_error", "wedge_version", "wedge_abi_sizes", "wedge_graph_build",
@@ -118,7 +147,9 @@ EXPORTS = ["wedge_status_str", "wedge_last_error", "wedge_version", "wedge_abi_s
            "wedge_bins_get_info", "wedge_bins_copy", "wedge_sample", "wedge_hoeffding_k", "wedge_estimate", "wedge_classify",
            "wedge_profile_enable", "wedge_profile_reset", "wedge_profile_read", "wedge_trim",
            "wedge_degree_offsets_noalloc", "wedge_batch_create", "wedge_batch_launch", "wedge_batch_results",
-           "wedge_batch_free", "wedge_batch_info", "wedge_sample_batch", "wedge_autotune"]
+           "wedge_batch_free", "wedge_batch_info", "wedge_sample_batch", "wedge_autotune", "wedge_server_create",
+           "wedge_server_destroy", "wedge_server_add_graph", "wedge_server_remove_graph", "wedge_server_submit",
+           "wedge_server_wait", "wedge_server_stats"]
 
 _lib = None
 
@@ -167,6 +198,13 @@ def load():
         "wedge_batch_info": ([P, P, P, P], st),
         "wedge_sample_batch": ([P, ctypes.c_int, P, P, P], st),
         "wedge_autotune": ([P, ctypes.c_int, P, P], st),
+        "wedge_server_create": ([P, P], st),
+        "wedge_server_destroy": ([P], None),
+        "wedge_server_add_graph": ([P, P, P, i64, i32, P], st),
+        "wedge_server_remove_graph": ([P, u64], st),
+        "wedge_server_submit": ([P, P, P], st),
+        "wedge_server_wait": ([P, u64, P, P], st),
+        "wedge_server_stats": ([P, P, ctypes.c_int], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -514,3 +552,68 @@ def autotune(requests: Requests, stream=None) -> LaunchConfig:
     c = LaunchConfig()
     _check(lib.wedge_autotune(requests.array, requests.n, _stream_handle(stream), ctypes.byref(c)))
     return c
+
+
+# ---------------------------------------------------------------------------
+# Serving (wedge_server_*)
+# ---------------------------------------------------------------------------
+
+class Server:
+    """Continuous-batching request loop over resident graphs."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 2, max_batch_requests: int = 0, tau: int = 1,
+                 omega: int = 2, launch=None):
+        lib = load()
+        c = ServerConfig()
+        c.hbm_budget_bytes = int(hbm_budget_bytes)
+        c.slots = int(slots)
+        c.max_batch_requests = int(max_batch_requests)
+        c.tau = int(tau)
+        c.omega = int(omega)
+        lc = _config(launch)
+        if lc is not None:
+            c.launch = lc
+        h = ctypes.c_void_p()
+        _check(lib.wedge_server_create(ctypes.byref(c), ctypes.byref(h)))
+        self._h = h.value
+
+    def add_graph(self, src, dst, n_vertices: int) -> int:
+        ps, ks = _ptr(src, np.int32)
+        pd, _ = _ptr(dst, np.int32)
+        gid = ctypes.c_uint64()
+        _check(load().wedge_server_add_graph(self._h, ps, pd, int(ks.shape[0]), int(n_vertices), ctypes.byref(gid)))
+        return gid.value
+
+    def remove_graph(self, graph_id: int):
+        _check(load().wedge_server_remove_graph(self._h, graph_id))
+
+    def submit(self, graph_id: int, seed: int, eps: float = 0.0, delta: float = 0.0, k_per_bin: int = 0,
+               k_global: int = 0, flags: int = 0) -> int:
+        r = ServerRequest(graph_id, seed, eps, delta, k_per_bin, k_global, flags, 0)
+        t = ctypes.c_uint64()
+        _check(load().wedge_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int):
+        c = CountsStruct()
+        tm = RequestTiming()
+        _check(load().wedge_server_wait(self._h, ticket, ctypes.byref(c), ctypes.byref(tm)))
+        return Counts(c), {"submit_us": tm.submit_us, "dispatch_us": tm.dispatch_us, "done_us": tm.done_us,
+                           "latency_us": tm.done_us - tm.submit_us, "batch_requests": tm.batch_requests}
+
+    def stats(self, reset: bool = False) -> dict:
+        m = ServerMetrics()
+        _check(load().wedge_server_stats(self._h, ctypes.byref(m), 1 if reset else 0))
+        return {f: (getattr(m, f) if not isinstance(getattr(m, f), int) else int(getattr(m, f)))
+                for f, _ in m._fields_ if f != "reserved"}
+
+    def close(self):
+        if self._h:
+            load().wedge_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

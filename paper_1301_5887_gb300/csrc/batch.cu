@@ -205,6 +205,7 @@ struct wedge_batch {
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;
   bool launched = false;
+  bool direct = false;  // enqueue the sequence on each launch instead of replaying a graph
 };
 
 namespace {
@@ -213,7 +214,7 @@ void batch_release(wedge_batch* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->done) cudaEventDestroy(b->done);
-  if (b->h_out) cudaFreeHost(b->h_out);
+  if (b->h_out) pinned_free(b->h_out, b->out_bytes);
   dfree(b->d_graphs, nullptr);
   dfree(b->d_streams, nullptr);
   dfree(b->d_tiles, nullptr);
@@ -369,12 +370,9 @@ extern "C" wedge_status wedge_batch_create(const wedge_request* reqs, int n_reqs
     return bail(st);
   if ((st = dalloc(reinterpret_cast<void**>(&b->d_out), b->out_bytes, s, "wedge_batch_create")) != WEDGE_OK)
     return bail(st);
-  cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_out), b->out_bytes, cudaHostAllocDefault);
-  if (e != cudaSuccess) {
-    b->h_out = nullptr;
-    cudaGetLastError();
-    return bail(fail(WEDGE_ENOMEM, "wedge_batch_create: cannot pin %zu host bytes", b->out_bytes));
-  }
+  b->h_out = static_cast<unsigned char*>(pinned_alloc(b->out_bytes));
+  if (!b->h_out) return bail(fail(WEDGE_ENOMEM, "wedge_batch_create: cannot pin %zu host bytes", b->out_bytes));
+  cudaError_t e = cudaSuccess;
   if (!graphs.empty()) {
     e = cudaMemcpyAsync(b->d_graphs, graphs.data(), graphs.size() * sizeof(BatchGraph), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return bail(cuda_fail(e, "wedge_batch_create"));
@@ -394,7 +392,8 @@ extern "C" wedge_status wedge_batch_create(const wedge_request* reqs, int n_reqs
   if (e != cudaSuccess) return bail(cuda_fail(e, "wedge_batch_create"));
 
   // Capture clear + kernel + copy-back once; every launch replays the graph.
-  if (b->n_tiles > 0) {
+  b->direct = (c.flags & WEDGE_BATCH_DIRECT) != 0;
+  if (b->n_tiles > 0 && !b->direct) {
     cudaStream_t cs = nullptr;
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(e, "wedge_batch_create: capture stream"));
@@ -419,7 +418,13 @@ extern "C" wedge_status wedge_batch_launch(wedge_batch* b, wedge_stream stream) 
   clear_error();
   if (!b) return fail(WEDGE_EINVAL, "wedge_batch_launch: NULL batch");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (b->exec) {
+  if (b->direct && b->n_tiles > 0) {
+    LaunchMark m = launch_begin("sample_batch", s);
+    wedge_status st = enqueue_batch(b, s);
+    wedge_status st2 = launch_end(m);
+    if (st != WEDGE_OK) return st;
+    if (st2 != WEDGE_OK) return st2;
+  } else if (b->exec) {
     LaunchMark m = launch_begin("sample_batch", s);
     cudaError_t e = cudaGraphLaunch(b->exec, s);
     wedge_status st = launch_end(m);
@@ -459,8 +464,7 @@ extern "C" wedge_status wedge_batch_results(wedge_batch* b, wedge_counts* out) {
 
 extern "C" void wedge_batch_free(wedge_batch* b) {
   if (!b) return;
-  if (b->launched) cudaEventSynchronize(b->done);
-  cudaDeviceSynchronize();
+  if (b->launched) cudaEventSynchronize(b->done);  // only this batch's work; other streams keep running
   batch_release(b);
 }
 

@@ -119,6 +119,41 @@ wedge_status trim_pool() {
   return WEDGE_OK;
 }
 
+namespace {
+std::mutex g_pin_mu;
+std::map<size_t, std::vector<void*>> g_pin_free;
+size_t pin_class(size_t bytes) {
+  size_t c = 4096;
+  while (c < bytes) c <<= 1;
+  return c;
+}
+}  // namespace
+
+void* pinned_alloc(size_t bytes) {
+  const size_t c = pin_class(bytes);
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    auto& v = g_pin_free[c];
+    if (!v.empty()) {
+      void* p = v.back();
+      v.pop_back();
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, c, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void pinned_free(void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free[pin_class(bytes)].push_back(p);
+}
+
 int sm_count() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 148;
@@ -179,11 +214,13 @@ const char* wedge_last_error(void) { return g_err; }
 uint32_t wedge_version(void) { return 0x000100u; }
 
 int wedge_abi_sizes(uint64_t* sizes, int cap) {
-  const uint64_t v[9] = {sizeof(wedge_graph_info), sizeof(wedge_bins_info),  sizeof(wedge_sample_params),
-                         sizeof(wedge_record),     sizeof(wedge_counts),     sizeof(wedge_estimates),
-                         sizeof(wedge_kernel_stat), sizeof(wedge_request),   sizeof(wedge_launch_config)};
-  for (int i = 0; i < 9 && i < cap && sizes; ++i) sizes[i] = v[i];
-  return 9;
+  const uint64_t v[13] = {sizeof(wedge_graph_info),    sizeof(wedge_bins_info),      sizeof(wedge_sample_params),
+                          sizeof(wedge_record),        sizeof(wedge_counts),         sizeof(wedge_estimates),
+                          sizeof(wedge_kernel_stat),   sizeof(wedge_request),        sizeof(wedge_launch_config),
+                          sizeof(wedge_server_config), sizeof(wedge_server_request), sizeof(wedge_request_timing),
+                          sizeof(wedge_server_metrics)};
+  for (int i = 0; i < 13 && i < cap && sizes; ++i) sizes[i] = v[i];
+  return 13;
 }
 
 const char* wedge_status_str(wedge_status st) {

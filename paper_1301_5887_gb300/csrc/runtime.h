@@ -36,6 +36,11 @@ wedge_status dalloc_n(T** p, size_t n, cudaStream_t s, const char* what) {
 
 int sm_count();
 
+// Pinned host blocks, cached by power-of-two size class and reused (pinning
+// and unpinning are slow and may synchronise the device).
+void* pinned_alloc(size_t bytes);
+void pinned_free(void* p, size_t bytes);
+
 // Launch accounting: every kernel launch goes through launch(), which counts
 // it and, when timing is enabled, brackets it with CUDA events on `s`.
 struct LaunchMark {
