@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests per rate for the serving sweep (the full sweep uses 10000; 0 skips it)")
+    ap.add_argument("--serve-rates", default="300,3000", help="arrival rates per second (full sweep: "
+                                                             "100,300,1000,3000,5000)")
     return ap.parse_args()
 
 
@@ -278,6 +282,128 @@ def bench_batched(wedge, graphgen, torch):
             "setup_s": setup_s, "tune_s": tune_s}
 
 
+def bench_serving(wedge, graphgen, torch, rates, n_requests, n_graphs=64, seed=5, upload_frac=0.01):
+    """Poisson request stream against a resident pool of Kronecker and
+    Chung-Lu graphs (scales 14-24) under a 150 GB HBM budget; per-request eps
+    drawn from {0.01, 0.005, 0.002}, delta 0.001; 1% of arrivals upload a new
+    edge list. For each rate: p50/p99 latency and Gwedges/s of the
+    continuous-batching server, against a plain path that runs the same
+    requests one wedge_sample call at a time in arrival order."""
+    import threading
+
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def gen_edges(i):
+        if i % 2 == 0:
+            scale = int(rng.integers(14, 25))
+            n, m = 1 << scale, graphgen.kronecker_edges(scale)
+            s = torch.empty(m, dtype=torch.int32, device="cuda")
+            d = torch.empty(m, dtype=torch.int32, device="cuda")
+            graphgen.kronecker_device(scale, s.data_ptr(), d.data_ptr(), m, stream, seed=40_000 + i)
+        else:
+            n = 1 << int(rng.integers(14, 25))
+            prefix, m = graphgen.chunglu_weights(n, float(rng.uniform(2.0, 2.6)), float(rng.uniform(8, 32)))
+            pd = torch.as_tensor(prefix.view(np.int64)).cuda()
+            s = torch.empty(m, dtype=torch.int32, device="cuda")
+            d = torch.empty(m, dtype=torch.int32, device="cuda")
+            graphgen.chunglu_device(pd.data_ptr(), n, s.data_ptr(), d.data_ptr(), m, 50_000 + i, stream_ptr=stream)
+        torch.cuda.synchronize()
+        return s, d, n
+
+    srv = wedge.Server(hbm_budget_bytes=150 * 10**9, slots=2,
+                       launch={"block_threads": 512, "samples_per_tile": 4096, "flags": wedge.BATCH_DIRECT})
+    ids, plain = [], []
+    for i in range(n_graphs):
+        s, d, n = gen_edges(i)
+        ids.append(srv.add_graph(s, d, n))
+        g = wedge.graph_build(s, d, n)
+        plain.append((g, wedge.bin(g, tau=TAU, omega=OMEGA)))
+        del s, d
+    torch.cuda.empty_cache()
+    eps_set = [0.01, 0.005, 0.002]
+    out = []
+    for rate in rates:
+        gaps = rng.exponential(1.0 / rate, n_requests)
+        arrivals = np.cumsum(gaps)
+        reqs = [(int(rng.integers(0, len(ids))), int(rng.integers(1, 1 << 40)), float(rng.choice(eps_set)),
+                 bool(rng.random() < upload_frac)) for _ in range(n_requests)]
+        # continuous-batching server
+        srv.stats(reset=True)
+        tickets = [None] * n_requests
+        uploads = []
+
+        def uploader(i):
+            s, d, n = gen_edges(1000 + i)
+            try:
+                t0 = time.perf_counter()
+                srv.add_graph(s, d, n)
+                uploads.append(time.perf_counter() - t0)
+            except wedge.WedgeError:
+                uploads.append(None)
+
+        up_threads = []
+        t_start = time.perf_counter()
+        for j, (gi, sd, eps, is_upload) in enumerate(reqs):
+            delay = t_start + arrivals[j] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            if is_upload:
+                th = threading.Thread(target=uploader, args=(j,))
+                th.start()
+                up_threads.append(th)
+            tickets[j] = srv.submit(ids[gi], sd, eps=eps, delta=0.001)
+        for t in tickets:
+            srv.wait(t)
+        for th in up_threads:
+            th.join()
+        st = srv.stats(reset=True)
+        # plain per-request path, same arrivals and uploads, one call at a time
+        lat = []
+        samples = 0
+        up_edges = [gen_edges(1000 + j) if reqs[j][3] else None for j in range(n_requests)]
+        t_start = time.perf_counter()
+        for j, (gi, sd, eps, is_upload) in enumerate(reqs):
+            delay = t_start + arrivals[j] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            if is_upload:
+                s_, d_, n_ = up_edges[j]
+                gu = wedge.graph_build(s_, d_, n_)
+                bu = wedge.bin(gu, tau=TAU, omega=OMEGA)
+                bu.free()
+                gu.free()
+                up_edges[j] = None
+            g, b = plain[gi]
+            c = wedge.sample(g, b, seed=sd, eps=eps, delta=0.001)
+            done = time.perf_counter()
+            lat.append((done - (t_start + arrivals[j])) * 1e6)
+            samples += int(c.k_b.sum()) + c.k_global
+        span = time.perf_counter() - t_start
+        lat.sort()
+
+        def pct(v, p):
+            return v[max(1, int(np.ceil(p * len(v)))) - 1]
+
+        out.append({"rate_per_s": rate, "requests": n_requests,
+                    "served": {"p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+                               "gwedges_per_s": st["samples"] / st["span_s"] / 1e9 if st["span_s"] else None,
+                               "requests_per_s": st["completed"] / st["span_s"] if st["span_s"] else None,
+                               "mean_batch_requests": st["mean_batch_requests"], "batches": st["batches"]},
+                    "plain": {"p50_ms": pct(lat, 0.5) / 1e3, "p99_ms": pct(lat, 0.99) / 1e3,
+                              "gwedges_per_s": samples / span / 1e9, "requests_per_s": n_requests / span},
+                    "uploads": len(uploads), "uploads_rejected": sum(1 for u in uploads if u is None)})
+    res_bytes = srv.stats()["resident_bytes"]
+    srv.close()
+    for g, b in plain:
+        b.free()
+        g.free()
+    return {"workload": f"{n_graphs} resident graphs (half Kronecker, half Chung-Lu, scales 14-24) under a 150 GB "
+                        f"budget; Poisson arrivals; eps in {{0.01, 0.005, 0.002}}, delta 0.001; "
+                        f"{upload_frac:.0%} uploads", "resident_bytes": res_bytes, "rates": out}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -412,6 +538,14 @@ def run_ours(args):
                "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
         del hsrc, hdst
 
+    serving = None
+    if args.serve_requests > 0:
+        wedge.trim()
+        torch.cuda.empty_cache()
+        serving = bench_serving(wedge, graphgen, torch, [float(r) for r in args.serve_rates.split(",")],
+                                args.serve_requests)
+        wedge.trim()
+
     batched = None
     if not args.no_batched:
         wedge.trim()
@@ -437,7 +571,7 @@ def run_ours(args):
                            "bins": info["n_bins"], "samples_per_step": info["samples"],
                            "l2": f"inputs {8 * n_edges / 1e9:.1f} GB > 129 MB L2, no flush needed",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "gwedges_checked_per_s": gwps, "sampling_ms": samp_ms, "batched": batched,
+                "gwedges_checked_per_s": gwps, "sampling_ms": samp_ms, "batched": batched, "serving": serving,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
                 "clocks": clk, "kernels": kernels,
                 "estimates": {"c_hat": info["c_hat"], "c_hat_global": info["c_hat_global"]}}
