@@ -172,6 +172,9 @@ WEDGE_API wedge_status wedge_bins_copy(const wedge_bins* b, int32_t* L, uint64_t
  * k_bin: optional host array of n_bins per-bin budgets indexed by bin id
  * (k_bin[b] samples for bin b; 0 skips the bin); when set it replaces
  * k_per_bin.
+ * first_sample: each stream draws sample indices [first_sample,
+ * first_sample + k); shards of one index range drawn on several GPUs sum
+ * (integer counters) to exactly the unsharded result.
  * records: optional device buffer of k_global wedge_record entries, written
  * for the global stream in sample order (NULL: none).
  * Errors: EINVAL if eps or delta is outside (0,1) while a budget is 0,
@@ -188,8 +191,9 @@ typedef struct {
   uint64_t k_per_bin;
   uint64_t k_global;
   uint32_t flags;
-  void* records;        /* device wedge_record[k_global] or NULL */
-  const uint64_t* k_bin; /* host uint64[n_bins] per-bin budgets or NULL */
+  void* records;          /* device wedge_record[k_global] or NULL (record i = sample first_sample + i) */
+  const uint64_t* k_bin;  /* host uint64[n_bins] per-bin budgets or NULL */
+  uint64_t first_sample;  /* first sample index of every stream (0 normally) */
 } wedge_sample_params;
 
 typedef struct {

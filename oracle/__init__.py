@@ -59,7 +59,7 @@ def _L():
         _lib.oracle_philox4x32_10.restype = None
         _lib.oracle_hoeffding_k.argtypes = [dbl, dbl]
         _lib.oracle_hoeffding_k.restype = u64
-        _lib.oracle_sample.argtypes = [i32, P, P, u32, u64, i32, u64, u64, u64, P, P, P, P, P]
+        _lib.oracle_sample.argtypes = [i32, P, P, u32, u64, i32, u64, u64, u64, P, P, P, P, P, u64]
         _lib.oracle_sample.restype = ctypes.c_int
         _lib.oracle_classify.argtypes = [i32, P, P, u32, u64, i64, P, P, P, P]
         _lib.oracle_classify.restype = ctypes.c_int
@@ -158,11 +158,12 @@ def hoeffding_k(eps: float, delta: float) -> int:
 # --------------------------------------------------------------------------
 
 def sample(off, adj, tau: int, omega: int, seed: int, k_per_bin: int, k_global: int, records: bool = False,
-           k_bins=None):
+           k_bins=None, first: int = 0):
     """Per-bin and global wedge sampling (Thm 3.2, Thm 3.3, Sec. 3.2) with the
     tally of Alg. Phase 4c. Returns counts[n_bins, 5] = (k_b, q0, q1, q2, q3),
     glob = (k_global, closed), stats[34, 34] and optional records[k_global, 8].
-    k_bins (optional, indexed by bin id) gives each bin its own budget."""
+    k_bins (optional, indexed by bin id) gives each bin its own budget; every
+    stream draws sample indices first .. first + k - 1."""
     off = _c(off, np.int64)
     adj = _c(adj, np.int32)
     n = off.shape[0] - 1
@@ -178,7 +179,7 @@ def sample(off, adj, tau: int, omega: int, seed: int, k_per_bin: int, k_global: 
         kb[: min(nb, src.shape[0])] = src[:nb]
     rc = _L().oracle_sample(n, _p(off), _p(adj), tau, omega, nb, seed, k_per_bin, k_global, _p(counts), _p(glob),
                             _p(stats), _p(rec) if records else ctypes.c_void_p(0),
-                            _p(kb) if kb is not None else ctypes.c_void_p(0))
+                            _p(kb) if kb is not None else ctypes.c_void_p(0), first)
     if rc != 0:
         raise RuntimeError(f"oracle_sample failed ({rc})")
     return {"counts": counts, "glob": glob, "stats": stats, "records": rec}

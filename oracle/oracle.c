@@ -251,11 +251,13 @@ static wedge_t draw_wedge(const int64_t* off, const int32_t* adj, const int32_t*
  * b < n_bins; glob[0..1] = (k_global, closed); stats[34*34] = closed global
  * wedges by (BinId22(d_min), BinId22(d_max)); rec (optional, 8 int32 per
  * global sample) = (v0, v1, v2, closed, d0, d1, d2, 0). k_bins (optional,
- * n_bins entries) gives each bin its own budget in place of k_per_bin.
+ * n_bins entries) gives each bin its own budget in place of k_per_bin. Every
+ * stream draws sample indices first .. first + k - 1.
  * Returns 0, -1 if n_bins is too small, -2 on allocation failure. */
 OR_EXPORT int oracle_sample(int32_t n, const int64_t* off, const int32_t* adj, uint32_t tau, uint64_t omega,
                             int32_t n_bins, uint64_t seed, uint64_t k_per_bin, uint64_t k_global,
-                            uint64_t* counts, uint64_t* glob, uint64_t* stats, int32_t* rec, const uint64_t* k_bins) {
+                            uint64_t* counts, uint64_t* glob, uint64_t* stats, int32_t* rec, const uint64_t* k_bins,
+                            uint64_t first) {
   for (int32_t b = 0; b < n_bins * 5; ++b) counts[b] = 0;
   glob[0] = glob[1] = 0;
   for (int i = 0; i < OR_STAT_BINS * OR_STAT_BINS; ++i) stats[i] = 0;
@@ -304,8 +306,9 @@ OR_EXPORT int oracle_sample(int32_t n, const int64_t* off, const int32_t* adj, u
     const uint64_t k = k_bins ? k_bins[b] : k_per_bin;
     uint64_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
 #pragma omp parallel for schedule(static) reduction(+ : q0, q1, q2, q3)
-    for (int64_t s = 0; s < (int64_t)k; ++s) {
-      const uint32_t ctr[4] = {(uint32_t)s, (uint32_t)((uint64_t)s >> 32), (uint32_t)b, 0u};
+    for (int64_t i = 0; i < (int64_t)k; ++i) {
+      const uint64_t s = first + (uint64_t)i;
+      const uint32_t ctr[4] = {(uint32_t)s, (uint32_t)(s >> 32), (uint32_t)b, 0u};
       const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
       uint32_t r[4];
       oracle_philox4x32_10(ctr, key, r);
@@ -344,8 +347,9 @@ OR_EXPORT int oracle_sample(int32_t n, const int64_t* off, const int32_t* adj, u
 #endif
       uint64_t* h = local + (size_t)tid * OR_STAT_BINS * OR_STAT_BINS;
 #pragma omp for schedule(static)
-      for (int64_t s = 0; s < (int64_t)k_global; ++s) {
-        const uint32_t ctr[4] = {(uint32_t)s, (uint32_t)((uint64_t)s >> 32), 0u, 1u};
+      for (int64_t i = 0; i < (int64_t)k_global; ++i) {
+        const uint64_t s = first + (uint64_t)i;
+        const uint32_t ctr[4] = {(uint32_t)s, (uint32_t)(s >> 32), 0u, 1u};
         const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
         uint32_t r[4];
         oracle_philox4x32_10(ctr, key, r);
@@ -360,7 +364,7 @@ OR_EXPORT int oracle_sample(int32_t n, const int64_t* off, const int32_t* adj, u
           h[oracle_bin_id(dmin, 2, 2) * OR_STAT_BINS + oracle_bin_id(dmax, 2, 2)] += 1;
         }
         if (rec) {
-          int32_t* o = rec + 8 * s;
+          int32_t* o = rec + 8 * i;
           o[0] = w.v0; o[1] = w.v1; o[2] = w.v2; o[3] = w.closed;
           o[4] = (int32_t)w.d0; o[5] = (int32_t)w.d1; o[6] = (int32_t)w.d2; o[7] = 0;
         }

@@ -68,7 +68,7 @@ class BinsInfo(ctypes.Structure):
 class SampleParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("eps", ctypes.c_double), ("delta", ctypes.c_double),
                 ("k_per_bin", ctypes.c_uint64), ("k_global", ctypes.c_uint64), ("flags", ctypes.c_uint32),
-                ("records", _vp), ("k_bin", _vp)]
+                ("records", _vp), ("k_bin", _vp), ("first_sample", ctypes.c_uint64)]
 
 
 class Record(ctypes.Structure):
@@ -388,14 +388,15 @@ def _budget_array(k_bin):
 
 
 def sample(graph: Graph, bins: Bins, seed: int, eps: float = 0.0, delta: float = 0.0, k_per_bin: int = 0,
-           k_global: int = 0, flags: int = 0, records=None, stream=None, k_bin=None) -> Counts:
-    """k_bin: optional per-bin budgets indexed by bin id (length >= n_bins)."""
+           k_global: int = 0, flags: int = 0, records=None, stream=None, k_bin=None, first_sample: int = 0) -> Counts:
+    """k_bin: optional per-bin budgets indexed by bin id (length >= n_bins);
+    first_sample: first sample index of every stream (for sharding)."""
     lib = load()
     kb = _budget_array(k_bin)
     if kb is not None and kb.shape[0] < bins.info().n_bins:
         raise ValueError("k_bin needs one entry per bin id")
     sp = SampleParams(seed, eps, delta, k_per_bin, k_global, flags, _ptr(records)[0] if records is not None else 0,
-                      kb.ctypes.data if kb is not None else 0)
+                      kb.ctypes.data if kb is not None else 0, first_sample)
     c = CountsStruct()
     _check(lib.wedge_sample(graph.handle, bins.handle, ctypes.byref(sp), _stream_handle(stream), ctypes.byref(c)))
     return Counts(c)
@@ -485,7 +486,7 @@ class Requests:
             self.array[i].params = SampleParams(it.get("seed", 0), it.get("eps", 0.0), it.get("delta", 0.0),
                                                 it.get("k_per_bin", 0), it.get("k_global", 0), it.get("flags", 0),
                                                 _ptr(rec)[0] if rec is not None else 0,
-                                                kb.ctypes.data if kb is not None else 0)
+                                                kb.ctypes.data if kb is not None else 0, it.get("first_sample", 0))
         self.items = items
 
 

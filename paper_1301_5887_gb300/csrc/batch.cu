@@ -41,6 +41,7 @@ struct BatchGraph {
 struct BatchStream {
   int64_t start, len;
   uint64_t p, wbase, k;
+  uint64_t first;  // first sample index
   uint32_t bin, tag;
   uint32_t req;
   uint32_t pad;
@@ -98,7 +99,8 @@ __global__ __launch_bounds__(THREADS) void k_sample_batch(const BatchGraph* __re
     const int step = per_warp ? WARPS : THREADS;
     const int me = per_warp ? warp : tid;
     for (int j = me; j < (int)tile.count; j += step) {
-      const uint64_t s = tile.first + (uint64_t)j;
+      const uint64_t local = tile.first + (uint64_t)j;
+      const uint64_t s = st.first + local;  // sample index in the stream
       const Philox4 r = philox4x32_10((uint32_t)s, (uint32_t)(s >> 32), st.bin, st.tag, g.seed_lo, g.seed_hi);
       const Wedge w = per_warp ? draw_wedge_warp(g.g, st.start, st.len, st.p, st.wbase, r, lane)
                                : draw_wedge_thread(g.g, st.start, st.len, st.p, st.wbase, r);
@@ -129,7 +131,7 @@ __global__ __launch_bounds__(THREADS) void k_sample_batch(const BatchGraph* __re
           rec.d1 = (int32_t)w.d1;
           rec.d2 = (int32_t)w.d2;
           rec.reserved = 0;
-          g.records[s] = rec;
+          g.records[local] = rec;
         }
       }
     }
@@ -321,6 +323,7 @@ extern "C" wedge_status wedge_batch_create(const wedge_request* reqs, int n_reqs
       st.p = p;
       st.wbase = wbase;
       st.k = k;
+      st.first = sp.first_sample;
       st.bin = bin;
       st.tag = tag;
       st.req = (uint32_t)r;

@@ -34,6 +34,7 @@ struct StreamDesc {
   uint64_t p;           // wedges in the stream
   uint64_t wbase;       // W[start]
   uint64_t k;           // samples to draw
+  uint64_t first;       // first sample index
   uint64_t tile_begin;  // first CTA of this stream
   uint32_t bin;         // Philox counter word 2 (bin id, 0 for the global stream)
   uint32_t tag;         // Philox counter word 3 (0 per-bin, 1 global)
@@ -81,8 +82,9 @@ __global__ __launch_bounds__(SAMPLE_THREADS) void k_sample(SampleArgs a) {
   const uint64_t first = ((uint64_t)blockIdx.x - desc.tile_begin) * SAMPLE_TILE;
   uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
   for (int j = 0; j < SAMPLE_PER_THREAD; ++j) {
-    const uint64_t s = first + (uint64_t)j * SAMPLE_THREADS + tid;
-    if (s >= desc.k) break;
+    const uint64_t local = first + (uint64_t)j * SAMPLE_THREADS + tid;
+    if (local >= desc.k) break;
+    const uint64_t s = desc.first + local;  // sample index in the stream
     const Philox4 r = philox4x32_10((uint32_t)s, (uint32_t)(s >> 32), desc.bin, desc.tag, a.seed_lo, a.seed_hi);
     const Wedge w = draw_wedge_thread(gv, desc.start, desc.len, desc.p, desc.wbase, r);
     const int32_t v0 = w.v0, v1 = w.v1, v2 = w.v2;
@@ -115,7 +117,7 @@ __global__ __launch_bounds__(SAMPLE_THREADS) void k_sample(SampleArgs a) {
         rec.d1 = (int32_t)d1;
         rec.d2 = (int32_t)d2;
         rec.reserved = 0;
-        a.records[s] = rec;
+        a.records[local] = rec;
       }
     }
   }
@@ -211,6 +213,7 @@ extern "C" wedge_status wedge_sample(const wedge_graph* g, const wedge_bins* b, 
     d.p = p;
     d.wbase = wbase;
     d.k = k;
+    d.first = sp->first_sample;
     d.tile_begin = tiles;
     d.bin = bin;
     d.tag = tag;

@@ -401,3 +401,25 @@ def test_kronecker_scale20_config():
         assert abs(est["c_b"][bb] - c_b) < eps
         assert abs(est["t_b"][bb] - t_b) < eps * pb
     assert abs(est["c_hat_global"] - 3 * ex["t"] / int(ex["p_b"].sum())) < eps
+
+
+def test_sharded_sample_ranges_sum_to_full():
+    """first_sample shards of every stream sum to the unsharded counts, and
+    records of a shard are the matching slice of the full records."""
+    from paper_1301_5887_gb300 import multi
+    s, d = _device_kronecker(12)
+    g = wedge.graph_build(s, d, 4096)
+    b = wedge.bin(g)
+    k = 30001
+    rec_full = torch.zeros((k, 8), dtype=torch.int32, device="cuda")
+    full = wedge.sample(g, b, seed=3, k_per_bin=k, k_global=k, records=rec_full)
+    tot = np.zeros_like(full.counts_matrix())
+    closed = 0
+    for r in range(4):
+        first, cnt = multi.shard_range(k, r, 4)
+        rec = torch.zeros((cnt, 8), dtype=torch.int32, device="cuda")
+        c = wedge.sample(g, b, seed=3, k_per_bin=cnt, k_global=cnt, first_sample=first, records=rec)
+        tot += c.counts_matrix()
+        closed += c.closed_global
+        assert torch.equal(rec, rec_full[first:first + cnt])
+    assert np.array_equal(tot, full.counts_matrix()) and closed == full.closed_global
