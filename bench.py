@@ -174,6 +174,38 @@ def run_reference(args):
 # Our arm
 # --------------------------------------------------------------------------
 
+KERNEL_SOURCES = {
+    # the sources a kernel's counters depend on; ncu figures are void once these change
+    "sort_onesweep_pass": ["sort.cu", "device.cuh"],
+    "sample_closure": ["sample.cu", "sample_device.cuh", "device.cuh"],
+    "dedup_rows": ["graph.cu", "device.cuh"],
+    "expand_edges": ["graph.cu"],
+    "probe_random_read": ["probe.cu"],
+}
+
+
+def source_hash(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(kernel, []):
+        with open(os.path.join(ROOT, "paper_1301_5887_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_figures(kernel):
+    """Counters of `kernel` from profiles/traffic.json if they were taken on
+    the current source, else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        ent = json.load(f).get(kernel)
+    if not ent or ent.get("source_hash") != source_hash(kernel):
+        return None
+    return ent
+
+
 ALG_BYTES = {
     # algorithmic DRAM bytes per launch, from the sizes of one step
     "sort_onesweep_pass": lambda z: 16 * z["nkeys"],
@@ -495,13 +527,9 @@ def run_ours(args):
     avg_ms = prof[top]["total_ms"] / prof[top]["launches"]
     achieved = ALG_BYTES[top](sizes) / (avg_ms / 1e3) / 1e9
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        with open(tfile) as f:
-            tr = json.load(f)
-        ent = tr.get(top)
-        if ent and ent.get("scale") and ent.get("bytes_per_launch"):
-            traffic = ent["bytes_per_launch"] * (sizes["nkeys"] / ent["nkeys"]) if "nkeys" in ent else None
+    ent = ncu_figures(top)
+    if ent and ent.get("bytes_per_unit"):  # DRAM read+write bytes per key (or edge), scaled to this launch
+        traffic = ent["bytes_per_unit"] * sizes[ent["unit"]]
     roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
@@ -510,6 +538,24 @@ def run_ours(args):
 
     kernels = {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["total_ms"] / args.steps,
                    "share": v["total_ms"] / max(ms_total, 1e-9)} for k, v in prof.items()}
+
+    # Sampling-stage roofline: the sampler's DRAM sector rate against the rate
+    # random reads can move sectors on this GPU. Random reads are probed live
+    # (accesses/s); sectors per sample and per probe access come from ncu
+    # counters taken on the current kernel sources (null otherwise).
+    wedge.trim()
+    probe = wedge.probe_random_read(32 << 30, 1 << 30)
+    sent, pent = ncu_figures("sample_closure"), ncu_figures("probe_random_read")
+    spl = sent["dram_sectors_per_sample"] if (sent and sent.get("scale") == scale) else None
+    spa = pent["dram_sectors_per_access"] if pent else None
+    ach = spl * info["samples"] / (samp_ms / 1e3) * 32 if (spl and samp_ms > 0) else None
+    peak = probe * spa * 32 if spa else None
+    sampling_roofline = {"bound": "random-sector", "kernel": "sample_closure", "unit": "GB/s",
+                         "achieved": ach / 1e9 if ach else None, "peak": peak / 1e9 if peak else None,
+                         "frac": ach / peak if (ach and peak) else None, "dram_sectors_per_sample": spl,
+                         "probe_accesses_per_s": probe, "probe_dram_sectors_per_access": spa,
+                         "peak_source": "wedge_probe_random_read live (2^30 independent 4-byte reads over 32 GB, "
+                                        "best of 3) x DRAM sectors per access from ncu"}
 
     # e2e: the same step from pinned host buffers through the C ABI.
     e2e = None
@@ -572,7 +618,7 @@ def run_ours(args):
                            "l2": f"inputs {8 * n_edges / 1e9:.1f} GB > 129 MB L2, no flush needed",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "gwedges_checked_per_s": gwps, "sampling_ms": samp_ms, "batched": batched, "serving": serving,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
+                "roofline": roofline, "sampling_roofline": sampling_roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
                 "clocks": clk, "kernels": kernels,
                 "estimates": {"c_hat": info["c_hat"], "c_hat_global": info["c_hat_global"]}}
         print(json.dumps(line), flush=True)

@@ -445,6 +445,14 @@ WEDGE_API void wedge_profile_reset(void);
 /* Fills up to cap entries; returns the number of kernels recorded. Synchronises pending events. */
 WEDGE_API int wedge_profile_read(wedge_kernel_stat* out, int cap);
 
+/* Measurement aid (no counterpart in the paper): the rate of independent
+ * random 4-byte reads, one 32-byte HBM sector each, over a fresh device
+ * buffer of buffer_bytes (use much more than L2), best of three runs of
+ * `reads` loads. The denominator of the sampling kernel's roofline.
+ * Allocates and frees the buffer; synchronises s. */
+WEDGE_API wedge_status wedge_probe_random_read(uint64_t buffer_bytes, uint64_t reads, wedge_stream s,
+                                               double* sectors_per_s);
+
 /* Release cached device memory of the library's pool on the current device. */
 WEDGE_API wedge_status wedge_trim(void);
 

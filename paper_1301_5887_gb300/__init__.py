@@ -149,7 +149,7 @@ EXPORTS = ["wedge_status_str", "wedge_last_error", "wedge_version", "wedge_abi_s
            "wedge_degree_offsets_noalloc", "wedge_batch_create", "wedge_batch_launch", "wedge_batch_results",
            "wedge_batch_free", "wedge_batch_info", "wedge_sample_batch", "wedge_autotune", "wedge_server_create",
            "wedge_server_destroy", "wedge_server_add_graph", "wedge_server_remove_graph", "wedge_server_submit",
-           "wedge_server_wait", "wedge_server_stats"]
+           "wedge_server_wait", "wedge_server_stats", "wedge_probe_random_read"]
 
 _lib = None
 
@@ -205,6 +205,7 @@ def load():
         "wedge_server_submit": ([P, P, P], st),
         "wedge_server_wait": ([P, u64, P, P], st),
         "wedge_server_stats": ([P, P, ctypes.c_int], st),
+        "wedge_probe_random_read": ([u64, u64, P, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -454,6 +455,13 @@ def profile_read() -> dict:
     n = lib.wedge_profile_read(arr, n)
     return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms)}
             for i in range(n)}
+
+
+def probe_random_read(buffer_bytes: int = 32 << 30, reads: int = 1 << 30, stream=None) -> float:
+    """Random 32-byte sector reads per second (wedge_probe_random_read)."""
+    r = ctypes.c_double()
+    _check(load().wedge_probe_random_read(buffer_bytes, reads, _stream_handle(stream), ctypes.byref(r)))
+    return r.value
 
 
 def trim():

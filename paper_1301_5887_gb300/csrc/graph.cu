@@ -96,32 +96,18 @@ __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restr
   }
   if (lane == 0) s_wcount[warp] = wcount;
   __syncthreads();
-  if (tid == 0) {
-    uint64_t tile_total = 0;
-    for (int w = 0; w < DEDUP_THREADS / 32; ++w) tile_total += s_wcount[w];
-    uint64_t* st = status + tile;
-    uint64_t excl = 0;
-    if (tile == 0) {
-      st_relaxed(st, lb_pack(1, LB_INC, tile_total));
-    } else {
-      st_relaxed(st, lb_pack(1, LB_AGG, tile_total));
-      excl = lookback(status, tile, 1, 1, err);
-      st_relaxed(st, lb_pack(1, LB_INC, excl + tile_total));
-    }
-    s_excl = excl;
-    if ((tile + 1) * DEDUP_TILE >= nkeys) *n_unique = (int64_t)(excl + tile_total);
-  }
-  __syncthreads();
-  uint64_t pos = s_excl;
-  for (int w = 0; w < warp; ++w) pos += s_wcount[w];
+  uint64_t tile_total = 0;
+  for (int w = 0; w < DEDUP_THREADS / 32; ++w) tile_total += s_wcount[w];
+  uint64_t* st = status + tile;
+  if (tid == 0) st_relaxed(st, lb_pack(1, tile == 0 ? LB_INC : LB_AGG, tile_total));  // publish early
+
+  // Row lengths first (they need no output position): sorted keys put equal
+  // sources in consecutive lanes; the last lane of each run adds the run's
+  // unique keys to its row's degree. Meanwhile thread 0 looks back.
   const uint32_t lt = lanemask_lt();
   const uint32_t le = lt | (1u << lane);
 #pragma unroll
   for (int i = 0; i < DEDUP_ITEMS; ++i) {
-    const bool f = (bal[i] >> lane) & 1u;
-    if (f) adj[pos + __popc(bal[i] & lt)] = (int32_t)(k[i] & vmask);
-    // Row lengths: sorted keys put equal sources in consecutive lanes. The
-    // last lane of each run adds the run's unique keys to its row's degree.
     const uint32_t u = (uint32_t)(k[i] >> b);
     const uint32_t u_prev = __shfl_up_sync(FULL_MASK, u, 1);
     const uint32_t u_next = __shfl_down_sync(FULL_MASK, u, 1);
@@ -132,6 +118,22 @@ __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restr
       const uint32_t c = __popc(bal[i] & le & ~((1u << start) - 1u));
       if (c) atomicAdd(deg + u, (int32_t)c);
     }
+  }
+  if (tid == 0) {
+    uint64_t excl = 0;
+    if (tile != 0) {
+      excl = lookback(status, tile, 1, 1, err);
+      st_relaxed(st, lb_pack(1, LB_INC, excl + tile_total));
+    }
+    s_excl = excl;
+    if ((tile + 1) * DEDUP_TILE >= nkeys) *n_unique = (int64_t)(excl + tile_total);
+  }
+  __syncthreads();
+  uint64_t pos = s_excl;
+  for (int w = 0; w < warp; ++w) pos += s_wcount[w];
+#pragma unroll
+  for (int i = 0; i < DEDUP_ITEMS; ++i) {
+    if ((bal[i] >> lane) & 1u) adj[pos + __popc(bal[i] & lt)] = (int32_t)(k[i] & vmask);
     pos += __popc(bal[i]);
   }
 }
