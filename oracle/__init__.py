@@ -61,6 +61,8 @@ def _L():
         _lib.oracle_hoeffding_k.restype = u64
         _lib.oracle_sample.argtypes = [i32, P, P, u32, u64, i32, u64, u64, u64, P, P, P, P, P, u64]
         _lib.oracle_sample.restype = ctypes.c_int
+        _lib.oracle_sample_rounding.argtypes = [i32, P, P, u32, u64, i32, u64, u64, P, P, P]
+        _lib.oracle_sample_rounding.restype = ctypes.c_int
         _lib.oracle_classify.argtypes = [i32, P, P, u32, u64, i64, P, P, P, P]
         _lib.oracle_classify.restype = ctypes.c_int
         _lib.oracle_exact.argtypes = [i32, P, P, u32, u64, i32, P, P]
@@ -183,6 +185,29 @@ def sample(off, adj, tau: int, omega: int, seed: int, k_per_bin: int, k_global: 
     if rc != 0:
         raise RuntimeError(f"oracle_sample failed ({rc})")
     return {"counts": counts, "glob": glob, "stats": stats, "records": rec}
+
+
+def sample_rounding(off, adj, tau: int, omega: int, seed: int, k_per_bin: int, k_bins=None, per_vertex=False):
+    """Per-bin samples allocated per vertex by probabilistic rounding (Alg.
+    Phase 2a) and drawn per centre (Alg. Phase 2c). Returns counts[n_bins, 5]
+    = (realised k_b, q0, q1, q2, q3) and, with per_vertex, q_v for every vertex."""
+    off = _c(off, np.int64)
+    adj = _c(adj, np.int32)
+    n = off.shape[0] - 1
+    nb = n_bins_for(off, tau, omega)
+    counts = np.zeros((nb, 5), np.uint64)
+    qv = np.zeros(n, np.uint64) if per_vertex else None
+    kb = None
+    if k_bins is not None:
+        kb = np.zeros(nb, np.uint64)
+        src = np.asarray(k_bins, dtype=np.uint64)
+        kb[: min(nb, src.shape[0])] = src[:nb]
+    rc = _L().oracle_sample_rounding(n, _p(off), _p(adj), tau, omega, nb, seed, k_per_bin,
+                                     _p(kb) if kb is not None else ctypes.c_void_p(0), _p(counts),
+                                     _p(qv) if per_vertex else ctypes.c_void_p(0))
+    if rc != 0:
+        raise RuntimeError(f"oracle_sample_rounding failed ({rc})")
+    return {"counts": counts, "qv": qv}
 
 
 def classify(off, adj, tau: int, omega: int, v0, v1, v2):

@@ -380,6 +380,94 @@ OR_EXPORT int oracle_sample(int32_t n, const int64_t* off, const int32_t* adj, u
   return 0;
 }
 
+/* Per-vertex allocation by probabilistic rounding (Alg. Phase 2a) and
+ * per-centre draws (Alg. Phase 2c, Procedure Sampling), the variant of the
+ * per-bin streams. For every vertex v with d = d_v >= 2, in bin b with wedge
+ * total p_b and budget k_b (k_bins[b], else k_per_bin):
+ *   q* = C(d,2) k_b / p_b, split exactly as floor F and remainder R
+ *     (C(d,2) k_b = F p_b + R, 0 <= R < p_b);
+ *   x: Philox counter (v, 0, 0, 2), t = floor((r0 + 2^32 r1) p_b / 2^64),
+ *     so x = t / p_b is uniform on a grid of [0,1);
+ *   q_v = F + [x < q* - F] = F + [t < R] (the text's rule: q* = 0.1 gives one
+ *     sample with probability 0.1).
+ * Then q_v wedges at v: the l-th (l = 0 .. q_v - 1) takes Philox counter
+ * (l mod 2^32, l div 2^32, v, 3), u = floor((r0 + 2^32 r1) d(d-1) / 2^64),
+ * i = u div (d-1), j' = u mod (d-1), j = j' + [j' >= i] (a uniform ordered pair
+ * of distinct neighbour indices), endpoints = the i-th and j-th neighbours.
+ * Each is tallied by Alg. Phase 4c; counts[b*5 + 0] is the bin's realised
+ * total sum_v q_v (the divisor of Alg. Phase 4c). qv (optional, n entries)
+ * receives q_v (0 for d < 2).
+ * Returns 0, -1 if n_bins is too small, -2 on allocation failure. */
+OR_EXPORT int oracle_sample_rounding(int32_t n, const int64_t* off, const int32_t* adj, uint32_t tau, uint64_t omega,
+                                     int32_t n_bins, uint64_t seed, uint64_t k_per_bin, const uint64_t* k_bins,
+                                     uint64_t* counts, uint64_t* qv) {
+  for (int32_t b = 0; b < n_bins * 5; ++b) counts[b] = 0;
+  uint64_t* p_b = (uint64_t*)calloc((size_t)n_bins, sizeof(uint64_t));
+  uint32_t* bin_of = (uint32_t*)malloc(sizeof(uint32_t) * ((size_t)n + 1));
+  if (!p_b || !bin_of) {
+    free(p_b); free(bin_of);
+    return -2;
+  }
+  for (int32_t v = 0; v < n; ++v) {
+    const uint64_t d = (uint64_t)(off[v + 1] - off[v]);
+    bin_of[v] = oracle_bin_id(d, tau, omega);
+    if (d >= 2) {
+      if ((int32_t)bin_of[v] >= n_bins) {
+        free(p_b); free(bin_of);
+        return -1;
+      }
+      p_b[bin_of[v]] += wedges_of(d);
+    }
+  }
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int32_t v = 0; v < n; ++v) {
+    const uint64_t d = (uint64_t)(off[v + 1] - off[v]);
+    if (qv) qv[v] = 0;
+    if (d < 2) continue;
+    const uint32_t b = bin_of[v];
+    const uint64_t k = k_bins ? k_bins[b] : k_per_bin;
+    const uint64_t p = p_b[b];
+    /* Phase 2a: q* and its probabilistic rounding */
+    const unsigned __int128 num = (unsigned __int128)wedges_of(d) * k;
+    const uint64_t F = (uint64_t)(num / p), R = (uint64_t)(num % p);
+    uint32_t r[4];
+    const uint32_t c_round[4] = {(uint32_t)v, 0u, 0u, 2u};
+    oracle_philox4x32_10(c_round, key, r);
+    const uint64_t t = mulhi64((uint64_t)r[0] | ((uint64_t)r[1] << 32), p);
+    const uint64_t q = F + (t < R ? 1 : 0);
+    if (qv) qv[v] = q;
+    counts[b * 5 + 0] += q;
+    /* Phase 2c: q wedges centred at v, each a uniform pair of distinct neighbours */
+    uint64_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+#pragma omp parallel for schedule(static) reduction(+ : q0, q1, q2, q3) if (q > 4096)
+    for (int64_t l = 0; l < (int64_t)q; ++l) {
+      const uint32_t c_draw[4] = {(uint32_t)l, (uint32_t)((uint64_t)l >> 32), (uint32_t)v, 3u};
+      uint32_t w[4];
+      oracle_philox4x32_10(c_draw, key, w);
+      const uint64_t dm1 = d - 1;
+      const uint64_t u = mulhi64((uint64_t)w[0] | ((uint64_t)w[1] << 32), d * dm1);
+      const uint64_t i = u / dm1, jp = u % dm1;
+      const uint64_t j = jp + (jp >= i ? 1 : 0);
+      const int32_t v1 = adj[off[v] + (int64_t)i], v2 = adj[off[v] + (int64_t)j];
+      /* Phase 3b closure, Phase 4c class */
+      if (!is_edge(off, adj, v1, v2)) {
+        q0 += 1;
+      } else {
+        const int c = 1 + (bin_of[v1] == b) + (bin_of[v2] == b);
+        if (c == 1) q1 += 1;
+        else if (c == 2) q2 += 1;
+        else q3 += 1;
+      }
+    }
+    counts[b * 5 + 1] += q0;
+    counts[b * 5 + 2] += q1;
+    counts[b * 5 + 3] += q2;
+    counts[b * 5 + 4] += q3;
+  }
+  free(p_b); free(bin_of);
+  return 0;
+}
+
 /* Closure and class of given wedges centred in bin b (Alg. Phase 3b, Alg.
  * Phase 4c): q[i] = 0 if open, else 1 + [BinId(d1)=b] + [BinId(d2)=b]. */
 OR_EXPORT int oracle_classify(int32_t n, const int64_t* off, const int32_t* adj, uint32_t tau, uint64_t omega,
