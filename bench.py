@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-rounding", action="store_true", help="skip the Phase 2a rounding-variant leg")
+    ap.add_argument("--tri-k", type=int, default=5_000_000,
+                    help="samples of the triangle-statistics leg (Sec. 5.7 single-bin run; 0 skips it)")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests per rate for the serving sweep (the full sweep uses 10000; 0 skips it)")
     ap.add_argument("--serve-rates", default="300,3000", help="arrival rates per second (full sweep: "
@@ -436,6 +439,54 @@ def bench_serving(wedge, graphgen, torch, rates, n_requests, n_graphs=64, seed=5
                         f"{upload_frac:.0%} uploads", "resident_bytes": res_bytes, "rates": out}
 
 
+def bench_rounding(wedge, graphgen, torch, g, b, iid_sampling_ms, reps=3, var_scale=18, var_seeds=24):
+    """Per-bin sampling by per-vertex probabilistic rounding (Alg. Phase 2a/2c)
+    against the i.i.d. inverse-CDF streams on the resident graph: time per
+    call (kernels from the profiler), and on a smaller graph the spread of the
+    per-bin estimates c_b over seeds for both allocations."""
+    import numpy as np
+    flags = wedge.FLAG_ROUNDING | wedge.FLAG_NO_GLOBAL
+    wedge.sample(g, b, seed=SEED, k_per_bin=K_SAMPLES, flags=flags)
+    wedge.profile_reset()
+    wedge.profile_enable(True)
+    for r in range(reps):
+        c = wedge.sample(g, b, seed=SEED + r, k_per_bin=K_SAMPLES, flags=flags)
+    wedge.profile_enable(False)
+    prof = wedge.profile_read()
+    names = ("round_alloc", "scan_round_counts", "round_bin_base", "round_draw")
+    per = {k: prof[k]["total_ms"] / reps for k in names if k in prof}
+    total_ms = sum(per.values())
+    samples = int(c.k_b.sum())
+    # estimator spread: same k per bin, many seeds, both allocations
+    s, d = graphgen.kronecker_host(var_scale, seed=2)
+    gs = wedge.graph_build(s, d, 1 << var_scale)
+    bs = wedge.bin(gs, tau=TAU, omega=OMEGA)
+    kv = 20000
+    est = {"iid": [], "rounding": []}
+    for seed in range(var_seeds):
+        ci = wedge.sample(gs, bs, seed=100 + seed, k_per_bin=kv, flags=wedge.FLAG_NO_GLOBAL)
+        cr = wedge.sample(gs, bs, seed=100 + seed, k_per_bin=kv, flags=flags)
+        for key, cc in (("iid", ci), ("rounding", cr)):
+            kb = cc.k_b.astype(np.float64)
+            closed = cc.q[:, 1:].sum(axis=1).astype(np.float64)
+            est[key].append(np.where(kb > 0, closed / np.maximum(kb, 1), np.nan))
+    spread = {}
+    for key in est:
+        a = np.array(est[key])
+        m = np.nanmean(a, axis=0)
+        sd = np.nanstd(a, axis=0, ddof=1)
+        ok = m > 0
+        spread[key] = float(np.nanmedian(sd[ok] / m[ok]))
+    bs.free()
+    gs.free()
+    return {"ms": total_ms, "kernels_ms": per, "samples": samples,
+            "gwedges_per_s": samples / (total_ms / 1e3) / 1e9 if total_ms > 0 else None,
+            "iid_sampling_ms_same_budget": iid_sampling_ms,
+            "median_rel_std_c_b": spread, "spread_workload": f"kronecker-s{var_scale}, k_b = {kv}, {var_seeds} seeds",
+            "note": "rounding: allocation + scan + bin bases + draws over the bins' streams (no global stream); "
+                    "iid_sampling_ms_same_budget includes the global stream's K samples as well"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -557,6 +608,35 @@ def run_ours(args):
                          "peak_source": "wedge_probe_random_read live (2^30 independent 4-byte reads over 32 GB, "
                                         "best of 3) x DRAM sectors per access from ncu"}
 
+    # Triangle statistics (Sec. 5.7): k global-stream samples, closed ones
+    # summarised per BinId(d_min); the call synchronises, so host time is device time.
+    tri = None
+    rounding = None
+    if args.tri_k > 0 or not args.no_rounding:
+        g = wedge.graph_build(src, dst, n)
+        b = wedge.bin(g, tau=TAU, omega=OMEGA)
+    if not args.no_rounding:
+        rounding = bench_rounding(wedge, graphgen, torch, g, b, samp_ms)
+    if args.tri_k > 0:
+        wedge.triangle_stats(g, b, SEED, args.tri_k)
+        times = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = wedge.triangle_stats(g, b, SEED, args.tri_k)
+            times.append(time.perf_counter() - t0)
+        med = sorted(times)[1]
+        groups = {int(i): {f: int(r["box"][i, j]) for j, f in enumerate(wedge.BOX_FIELDS)}
+                  for i in range(r["box"].shape[0]) if r["box"][i, 0]}
+        tri = {"k": args.tri_k, "closed": r["closed"], "ms": med * 1e3, "samples_per_s": args.tri_k / med,
+               "ratio_q": [float(x) for x in r["ratio_q"]], "box_by_dmin_bin": groups,
+               "note": "median of 3 calls of wedge_triangle_stats on the resident graph (sampling with records, "
+                       "key compaction, two radix sorts, box plots)"}
+    if args.tri_k > 0 or not args.no_rounding:
+        b.free()
+        g.free()
+        wedge.trim()
+
     # e2e: the same step from pinned host buffers through the C ABI.
     e2e = None
     if args.e2e_steps > 0:
@@ -618,7 +698,7 @@ def run_ours(args):
                            "l2": f"inputs {8 * n_edges / 1e9:.1f} GB > 129 MB L2, no flush needed",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "gwedges_checked_per_s": gwps, "sampling_ms": samp_ms, "batched": batched, "serving": serving,
-                "roofline": roofline, "sampling_roofline": sampling_roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
+                "triangle_stats": tri, "rounding": rounding, "roofline": roofline, "sampling_roofline": sampling_roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
                 "clocks": clk, "kernels": kernels,
                 "estimates": {"c_hat": info["c_hat"], "c_hat_global": info["c_hat_global"]}}
         print(json.dumps(line), flush=True)

@@ -67,7 +67,8 @@ WEDGE_API uint32_t wedge_version(void);
 /* sizeof of the ABI structs, for bindings to check their layouts: fills up to
  * cap of [graph_info, bins_info, sample_params, record, counts, estimates,
  * kernel_stat, request, launch_config, server_config, server_request,
- * request_timing, server_metrics] and returns 13. */
+ * request_timing, server_metrics, triangle_box, triangle_summary] and
+ * returns 15. */
 WEDGE_API int wedge_abi_sizes(uint64_t* sizes, int cap);
 
 /* --------------------------------------------------------------------------
@@ -177,12 +178,28 @@ WEDGE_API wedge_status wedge_bins_copy(const wedge_bins* b, int32_t* L, uint64_t
  * (integer counters) to exactly the unsharded result.
  * records: optional device buffer of k_global wedge_record entries, written
  * for the global stream in sample order (NULL: none).
+ *
+ * WEDGE_FLAG_ROUNDING replaces the per-bin streams by the allocation of
+ * Alg. Phase 2a and the per-centre draws of Alg. Phase 2c: every vertex v of
+ * degree d >= 2 in bin b gets q_v = floor(q*) + [x < q* - floor(q*)] samples,
+ * q* = C(d,2) k_b / p_b, x uniform in [0,1) (so E[q_v] = q*; the bin's total is
+ * random with mean k_b), and q_v wedges centred at v are drawn independently,
+ * each a uniform pair of distinct neighbours. Random words: the rounding of v
+ * uses Philox counter (v, 0, 0, 2), x = floor((r0 + 2^32 r1) p_b / 2^64) / p_b,
+ * round up iff floor((r0 + 2^32 r1) p_b / 2^64) < (C(d,2) k_b mod p_b); the
+ * l-th wedge at v uses counter (l mod 2^32, l div 2^32, v, 3), pair index
+ * u = floor((r0 + 2^32 r1) d(d-1) / 2^64) mapped to (i, j) as above. The tally
+ * is Alg. Phase 4c's and counts.k_b is the bin's realised total sum_v q_v,
+ * the divisor of Alg. Phase 4c. The global stream is unchanged.
+ *
  * Errors: EINVAL if eps or delta is outside (0,1) while a budget is 0,
- * bins do not belong to g, or records is set with WEDGE_FLAG_NO_GLOBAL;
- * ECUDA; ENOMEM.
+ * bins do not belong to g, records is set with WEDGE_FLAG_NO_GLOBAL, or
+ * WEDGE_FLAG_ROUNDING is combined with first_sample != 0; ECUDA; ENOMEM;
+ * ETIMEOUT (rounding: a scan look-back wait gave up).
  * ------------------------------------------------------------------------ */
 #define WEDGE_FLAG_NO_GLOBAL 0x1u  /* skip the global stream */
 #define WEDGE_FLAG_NO_BINS 0x2u    /* skip the per-bin streams */
+#define WEDGE_FLAG_ROUNDING 0x4u   /* per-bin samples allocated per vertex (Alg. Phase 2a) */
 
 typedef struct {
   uint64_t seed;
@@ -402,6 +419,49 @@ WEDGE_API wedge_status wedge_estimate(const wedge_counts* c, double delta, wedge
  * ------------------------------------------------------------------------ */
 WEDGE_API wedge_status wedge_classify(const wedge_graph* g, const wedge_bins* b, int64_t n_wedges, const int32_t* v0,
                             const int32_t* v1, const int32_t* v2, uint8_t* q, wedge_stream s);
+
+/* --------------------------------------------------------------------------
+ * Triangle statistics from sampled wedges (Sec. 5.7, Thm 3.4).
+ *
+ * Draws samples [0, k) of the global stream (wedges uniform over all wedges,
+ * the paper's single-bin run; identical to wedge_sample's global stream with
+ * the same seed). The closed ones are a uniform sample of triangles, each
+ * with a smallest and a largest vertex degree d_min <= d_max. Grouped by
+ * BinId(d_min) with tau = 2, omega = 2 (d for d <= 2, else 1 + the bit length
+ * of d - 1), each group's d_max values are summarised as a box plot:
+ *   q1, median, q3: nearest-rank percentiles, the ceil(p c)-th smallest of
+ *     the group's c values for p = 1/4, 1/2, 3/4;
+ *   whisker_lo / whisker_hi: the smallest / largest value v of the group
+ *     with q1 - 1.5 (q3 - q1) <= v <= q3 + 1.5 (q3 - q1), compared exactly;
+ *   outliers: the number of values outside those bounds.
+ * ratio_q holds min, q1, median, q3, max (same nearest-rank rule) of the
+ * FP64 ratio d_max / d_min (a correctly rounded division) over all closed
+ * samples; hist is the (BinId(d_min), BinId(d_max)) histogram of the same
+ * closed samples (wedge_counts.stats). closed estimates k times the global
+ * clustering coefficient.
+ *   records: optional device wedge_record[k] to receive every sample's
+ *     record (raw (d_min, d_mid, d_max) per triangle); NULL: scratch only.
+ *   Synchronises s. Results are deterministic (integer order statistics).
+ *   Errors: EINVAL for NULL handles, bins of another graph, k = 0 or
+ *   k > 2^34; ENOMEM; ECUDA; ETIMEOUT.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  uint64_t count; /* closed samples whose d_min lies in this bin */
+  uint64_t min, q1, median, q3, max;
+  uint64_t whisker_lo, whisker_hi;
+  uint64_t outliers;
+} wedge_triangle_box;
+
+typedef struct {
+  uint64_t k;
+  uint64_t closed;
+  wedge_triangle_box box[WEDGE_STAT_BINS]; /* indexed by BinId(d_min) */
+  double ratio_q[5];
+  uint64_t hist[WEDGE_STAT_BINS][WEDGE_STAT_BINS];
+} wedge_triangle_summary;
+
+WEDGE_API wedge_status wedge_triangle_stats(const wedge_graph* g, const wedge_bins* b, uint64_t seed, uint64_t k,
+                                            void* records, wedge_stream s, wedge_triangle_summary* out);
 
 /* --------------------------------------------------------------------------
  * Allocation-free CSR row offsets. The paper has no counterpart: this entry

@@ -30,6 +30,7 @@ MAX_BINS = 256
 STAT_BINS = 34
 FLAG_NO_GLOBAL = 0x1
 FLAG_NO_BINS = 0x2
+FLAG_ROUNDING = 0x4  # per-bin samples allocated per vertex by probabilistic rounding (Alg. Phase 2a)
 
 STATUS = {0: "WEDGE_OK", 1: "WEDGE_EINVAL", 2: "WEDGE_ENOMEM", 3: "WEDGE_ECUDA", 4: "WEDGE_ETIMEOUT",
           5: "WEDGE_EOVERFLOW"}
@@ -138,8 +139,18 @@ class ServerMetrics(ctypes.Structure):
                 ("rejected_uploads", ctypes.c_uint64)]
 
 
+class TriangleBox(ctypes.Structure):
+    _fields_ = [(x, ctypes.c_uint64) for x in ("count", "min", "q1", "median", "q3", "max", "whisker_lo",
+                                                "whisker_hi", "outliers")]
+
+
+class TriangleSummary(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint64), ("closed", ctypes.c_uint64), ("box", TriangleBox * STAT_BINS),
+                ("ratio_q", ctypes.c_double * 5), ("hist", (ctypes.c_uint64 * STAT_BINS) * STAT_BINS)]
+
+
 _STRUCTS = [GraphInfo, BinsInfo, SampleParams, Record, CountsStruct, EstimatesStruct, KernelStat, Request,
-            LaunchConfig, ServerConfig, ServerRequest, RequestTiming, ServerMetrics]
+            LaunchConfig, ServerConfig, ServerRequest, RequestTiming, ServerMetrics, TriangleBox, TriangleSummary]
 
 # Every symbol include/wedge.h declares.
 EXPORTS = ["wedge_status_str", "wedge_last_error", "wedge_version", "wedge_abi_sizes", "wedge_graph_build",
@@ -149,7 +160,7 @@ EXPORTS = ["wedge_status_str", "wedge_last_error", "wedge_version", "wedge_abi_s
            "wedge_degree_offsets_noalloc", "wedge_batch_create", "wedge_batch_launch", "wedge_batch_results",
            "wedge_batch_free", "wedge_batch_info", "wedge_sample_batch", "wedge_autotune", "wedge_server_create",
            "wedge_server_destroy", "wedge_server_add_graph", "wedge_server_remove_graph", "wedge_server_submit",
-           "wedge_server_wait", "wedge_server_stats", "wedge_probe_random_read"]
+           "wedge_server_wait", "wedge_server_stats", "wedge_probe_random_read", "wedge_triangle_stats"]
 
 _lib = None
 
@@ -206,13 +217,14 @@ def load():
         "wedge_server_wait": ([P, u64, P, P], st),
         "wedge_server_stats": ([P, P, ctypes.c_int], st),
         "wedge_probe_random_read": ([u64, u64, P, P], st),
+        "wedge_triangle_stats": ([P, P, u64, u64, P, P, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = res
-    sizes = (ctypes.c_uint64 * 16)()
-    lib.wedge_abi_sizes(sizes, 16)
+    sizes = (ctypes.c_uint64 * 32)()
+    lib.wedge_abi_sizes(sizes, 32)
     for i, S in enumerate(_STRUCTS):
         if sizes[i] != ctypes.sizeof(S):
             raise ImportError(f"ABI mismatch for {S.__name__}: C {sizes[i]} bytes, binding {ctypes.sizeof(S)}")
@@ -422,6 +434,29 @@ def classify(graph: Graph, bins: Bins, v0, v1, v2, q, stream=None):
     pq, _ = _ptr(q, np.uint8)
     n = int(k0.shape[0])
     _check(lib.wedge_classify(graph.handle, bins.handle, n, p0, p1, p2, pq, _stream_handle(stream)))
+
+
+BOX_FIELDS = ("count", "min", "q1", "median", "q3", "max", "whisker_lo", "whisker_hi", "outliers")
+
+
+def triangle_stats(graph: Graph, bins: Bins, seed: int, k: int, records=None, stream=None) -> dict:
+    """Sampled-triangle statistics (wedge_triangle_stats): k global-stream
+    samples; "box" is (34, 9) uint64 with columns BOX_FIELDS per BinId(d_min),
+    "ratio_q" the min, q1, median, q3, max of d_max / d_min, "hist" the
+    (BinId(d_min), BinId(d_max)) histogram. records: optional device buffer of
+    k * 8 int32 to receive the per-sample records."""
+    lib = load()
+    out = TriangleSummary()
+    pr = 0
+    if records is not None:
+        pr, arr = _ptr(records, np.int32)
+        if int(np.prod(arr.shape)) < 8 * k:
+            raise ValueError("records needs k * 8 int32 entries")
+    _check(lib.wedge_triangle_stats(graph.handle, bins.handle, seed, k, pr, _stream_handle(stream),
+                                    ctypes.byref(out)))
+    box = np.array([[getattr(out.box[i], f) for f in BOX_FIELDS] for i in range(STAT_BINS)], np.uint64)
+    return {"k": int(out.k), "closed": int(out.closed), "box": box, "ratio_q": np.array(out.ratio_q[:], np.float64),
+            "hist": np.array([list(out.hist[i]) for i in range(STAT_BINS)], np.uint64)}
 
 
 NOALLOC_MAX_VERTICES = 536870912

@@ -52,6 +52,15 @@ wedge_status scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, void* 
                              cudaStream_t s);
 wedge_status scan_u64_to_u64(const uint64_t* in, uint64_t* out, int64_t n, void* scratch, uint32_t* derr,
                              cudaStream_t s);
+// out[i] = sum in[0..i) for i < n and out[n] = the total (out holds n + 1).
+wedge_status scan_u64_with_total(const uint64_t* in, uint64_t* out, int64_t n, void* scratch, uint32_t* derr,
+                                 cudaStream_t s, const char* name);
+
+// Per-bin samples allocated per vertex by probabilistic rounding and drawn per
+// centre (rounding.cu). k_of_bin: host, n_bins budgets. Fills out->k_b (the
+// realised totals) and out->q for every bin; synchronises s.
+wedge_status sample_rounding(const wedge_graph* g, const wedge_bins* b, uint64_t seed, const uint64_t* k_of_bin,
+                             cudaStream_t s, wedge_counts* out);
 
 uint64_t next_uid();
 

@@ -181,9 +181,8 @@ extern "C" uint64_t wedge_hoeffding_k(double eps, double delta) {
   return (uint64_t)std::ceil(std::log(2.0 / delta) / (2.0 * eps * eps));
 }
 
-extern "C" wedge_status wedge_sample(const wedge_graph* g, const wedge_bins* b, const wedge_sample_params* sp,
-                                     wedge_stream stream, wedge_counts* out) {
-  clear_error();
+static wedge_status sample_streams(const wedge_graph* g, const wedge_bins* b, const wedge_sample_params* sp,
+                                   wedge_stream stream, wedge_counts* out) {
   if (!g || !b || !sp || !out) return fail(WEDGE_EINVAL, "wedge_sample: NULL argument");
   if (b->graph_uid != g->uid) return fail(WEDGE_EINVAL, "wedge_sample: bins were built from another graph");
   const bool want_bins = !(sp->flags & WEDGE_FLAG_NO_BINS);
@@ -330,4 +329,28 @@ extern "C" wedge_status wedge_classify(const wedge_graph* g, const wedge_bins* b
   dfree(derr, s);
   if (st == WEDGE_OK && (herr & DERR_BAD_ID)) st = fail(WEDGE_EINVAL, "wedge_classify: a vertex id is outside [0, n)");
   return st;
+}
+
+extern "C" wedge_status wedge_sample(const wedge_graph* g, const wedge_bins* b, const wedge_sample_params* sp,
+                                     wedge_stream stream, wedge_counts* out) {
+  clear_error();
+  if (!g || !b || !sp || !out) return fail(WEDGE_EINVAL, "wedge_sample: NULL argument");
+  const bool rounding = (sp->flags & WEDGE_FLAG_ROUNDING) && !(sp->flags & WEDGE_FLAG_NO_BINS);
+  if (!rounding) return sample_streams(g, b, sp, stream, out);
+  // Alg. Phase 2a variant: the global stream as usual, then the bins by rounding.
+  if (sp->first_sample != 0) return fail(WEDGE_EINVAL, "wedge_sample: WEDGE_FLAG_ROUNDING needs first_sample = 0");
+  if (b->graph_uid != g->uid) return fail(WEDGE_EINVAL, "wedge_sample: bins were built from another graph");
+  uint64_t k_bin = sp->k_per_bin;
+  if (k_bin == 0 && !sp->k_bin) {
+    k_bin = wedge_hoeffding_k(sp->eps, sp->delta);
+    if (k_bin == 0) return fail(WEDGE_EINVAL, "wedge_sample: eps and delta must lie in (0, 1) when a budget is 0");
+  }
+  wedge_sample_params rest = *sp;
+  rest.flags |= WEDGE_FLAG_NO_BINS;
+  wedge_status st = sample_streams(g, b, &rest, stream, out);
+  if (st != WEDGE_OK) return st;
+  const uint32_t nb = b->info.n_bins;
+  std::vector<uint64_t> k_of_bin(nb);
+  for (uint32_t k = 0; k < nb; ++k) k_of_bin[k] = sp->k_bin ? sp->k_bin[k] : k_bin;
+  return sample_rounding(g, b, sp->seed, k_of_bin.data(), reinterpret_cast<cudaStream_t>(stream), out);
 }

@@ -144,6 +144,11 @@ wedge_status scan_u64_to_u64(const uint64_t* in, uint64_t* out, int64_t n, void*
   return run_scan<uint64_t, uint64_t>(in, out, n, nullptr, nullptr, scratch, derr, s, "scan_bin_wedges");
 }
 
+wedge_status scan_u64_with_total(const uint64_t* in, uint64_t* out, int64_t n, void* scratch, uint32_t* derr,
+                                 cudaStream_t s, const char* name) {
+  return run_scan<uint64_t, uint64_t>(in, out, n, out + n, nullptr, scratch, derr, s, name);
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free row offsets (wedge_degree_offsets_noalloc).
 //
