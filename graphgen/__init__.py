@@ -34,7 +34,8 @@ def build_host(force: bool = False) -> str:
     src = os.path.join(_HERE, "gen_host.c")
     if force or not _fresh(_HOST_SO, [src, _HDR]):
         tmp = _HOST_SO + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared", "-Wall", "-o", tmp, src, "-lm"],
+        subprocess.run(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-Wall", "-o",
+                        tmp, src, "-lm"],
                        check=True)
         os.replace(tmp, _HOST_SO)
     return _HOST_SO
@@ -69,6 +70,10 @@ def _H():
         _host.graphgen_chunglu_weights.restype = i64
         _host.graphgen_chunglu_host.argtypes = [P, u64, i64, i64, u64, ctypes.c_int, P, P]
         _host.graphgen_chunglu_host.restype = ctypes.c_int
+        _host.graphgen_rmat_noisy_levels.argtypes = [u32, dbl, dbl, dbl, dbl, u64, P]
+        _host.graphgen_rmat_noisy_levels.restype = ctypes.c_int
+        _host.graphgen_kronecker_levels_host.argtypes = [u32, i64, i64, P, u64, ctypes.c_int, P, P]
+        _host.graphgen_kronecker_levels_host.restype = ctypes.c_int
         _host.graphgen_permute_host.argtypes = [u64, u64, i64, P, P]
         _host.graphgen_permute_host.restype = ctypes.c_int
     return _host
@@ -81,6 +86,8 @@ def _D():
         P, i64, u32, u64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
         _cuda.graphgen_kronecker_device.argtypes = [u32, i64, dbl, dbl, dbl, u64, ctypes.c_int, P, P, P]
         _cuda.graphgen_kronecker_device.restype = ctypes.c_int
+        _cuda.graphgen_kronecker_levels_device.argtypes = [u32, i64, P, u64, ctypes.c_int, P, P, P]
+        _cuda.graphgen_kronecker_levels_device.restype = ctypes.c_int
         _cuda.graphgen_chunglu_device.argtypes = [P, u64, i64, u64, ctypes.c_int, P, P, P]
         _cuda.graphgen_chunglu_device.restype = ctypes.c_int
     return _cuda
@@ -94,24 +101,46 @@ def kronecker_edges(scale: int, edgefactor: int = EDGEFACTOR) -> int:
     return edgefactor << scale
 
 
+def rmat_levels(scale: int, noise: float, seed: int = 1, a: float = RMAT_A, b: float = RMAT_B, c: float = RMAT_C):
+    """Integer quadrant thresholds (scale, 3) of the noisy SKG levels (noise 0: the plain matrix at every level)."""
+    th = np.zeros((scale, 3), np.uint32)
+    if _H().graphgen_rmat_noisy_levels(scale, a, b, c, noise, seed, _ptr(th)) != 0:
+        raise ValueError("graphgen_rmat_noisy_levels: bad arguments")
+    return th
+
+
 def kronecker_host(scale: int, n_edges: int | None = None, seed: int = 1, permute: bool = True,
-                   a: float = RMAT_A, b: float = RMAT_B, c: float = RMAT_C, e0: int = 0):
-    """Edges [e0, e0 + n_edges) of the R-MAT graph with 2^scale vertices (host int32 arrays)."""
+                   a: float = RMAT_A, b: float = RMAT_B, c: float = RMAT_C, e0: int = 0, noise: float = 0.0):
+    """Edges [e0, e0 + n_edges) of the R-MAT graph with 2^scale vertices (host int32 arrays).
+    noise > 0: noisy SKG with that noise parameter (the paper uses 0.1)."""
     if n_edges is None:
         n_edges = kronecker_edges(scale)
     src = np.empty(n_edges, np.int32)
     dst = np.empty(n_edges, np.int32)
-    rc = _H().graphgen_kronecker_host(scale, e0, e0 + n_edges, a, b, c, seed, int(permute), _ptr(src), _ptr(dst))
+    if noise > 0:
+        th = rmat_levels(scale, noise, seed, a, b, c)
+        rc = _H().graphgen_kronecker_levels_host(scale, e0, e0 + n_edges, _ptr(th), seed, int(permute), _ptr(src),
+                                                 _ptr(dst))
+    else:
+        rc = _H().graphgen_kronecker_host(scale, e0, e0 + n_edges, a, b, c, seed, int(permute), _ptr(src),
+                                          _ptr(dst))
     if rc != 0:
         raise ValueError("graphgen_kronecker_host: bad arguments")
     return src, dst
 
 
 def kronecker_device(scale: int, src_ptr: int, dst_ptr: int, n_edges: int, stream_ptr: int = 0, seed: int = 1,
-                     permute: bool = True, a: float = RMAT_A, b: float = RMAT_B, c: float = RMAT_C):
+                     permute: bool = True, a: float = RMAT_A, b: float = RMAT_B, c: float = RMAT_C,
+                     noise: float = 0.0):
     """Same edges as kronecker_host, written to device buffers (raw pointers)."""
-    rc = _D().graphgen_kronecker_device(scale, n_edges, a, b, c, seed, int(permute), ctypes.c_void_p(src_ptr),
-                                        ctypes.c_void_p(dst_ptr), ctypes.c_void_p(stream_ptr))
+    if noise > 0:
+        th = rmat_levels(scale, noise, seed, a, b, c)
+        rc = _D().graphgen_kronecker_levels_device(scale, n_edges, _ptr(th), seed, int(permute),
+                                                   ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr),
+                                                   ctypes.c_void_p(stream_ptr))
+    else:
+        rc = _D().graphgen_kronecker_device(scale, n_edges, a, b, c, seed, int(permute), ctypes.c_void_p(src_ptr),
+                                            ctypes.c_void_p(dst_ptr), ctypes.c_void_p(stream_ptr))
     if rc != 0:
         raise RuntimeError(f"graphgen_kronecker_device failed (cudaError {rc})")
 

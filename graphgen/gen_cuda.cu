@@ -27,6 +27,26 @@ __global__ void kronecker_kernel(gg_rmat_thresholds th, uint32_t scale, uint64_t
   }
 }
 
+struct LevelTable {
+  gg_rmat_thresholds lv[32];
+};
+
+__global__ void kronecker_levels_kernel(LevelTable th, uint32_t scale, uint64_t edge_seed, gg_perm perm,
+                                        int permute, int64_t n_edges, int32_t* __restrict__ src,
+                                        int32_t* __restrict__ dst) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_edges; e += stride) {
+    uint64_t u, v;
+    gg_rmat_edge_levels(th.lv, scale, edge_seed, (uint64_t)e, &u, &v);
+    if (permute) {
+      u = gg_perm_apply(&perm, u);
+      v = gg_perm_apply(&perm, v);
+    }
+    src[e] = (int32_t)u;
+    dst[e] = (int32_t)v;
+  }
+}
+
 __global__ void chunglu_kernel(const uint64_t* __restrict__ prefix, uint64_t n, uint64_t cl_seed, gg_perm perm,
                                int permute, int64_t n_edges, int32_t* __restrict__ src,
                                int32_t* __restrict__ dst) {
@@ -65,6 +85,25 @@ GG_EXPORT int graphgen_kronecker_device(uint32_t scale, int64_t n_edges, double 
   const gg_perm perm = gg_perm_make(1ULL << scale, seed);
   kronecker_kernel<<<grid_for(n_edges), 256, 0, stream>>>(th, scale, gg_stream_seed(seed, GG_STREAM_EDGES), perm,
                                                           permute, n_edges, src, dst);
+  return (int)cudaGetLastError();
+}
+
+// Kronecker edges with per-level thresholds th[3 scale] (host array, from
+// graphgen_rmat_noisy_levels); same edges as graphgen_kronecker_levels_host.
+GG_EXPORT int graphgen_kronecker_levels_device(uint32_t scale, int64_t n_edges, const uint32_t* th, uint64_t seed,
+                                               int permute, int32_t* src, int32_t* dst, cudaStream_t stream) {
+  if (scale < 1 || scale > 31 || n_edges < 0 || !th || (n_edges > 0 && (!src || !dst)))
+    return (int)cudaErrorInvalidValue;
+  if (n_edges == 0) return 0;
+  LevelTable t;
+  for (uint32_t l = 0; l < 32; ++l) {
+    t.lv[l].t_a = l < scale ? th[3 * l] : 0u;
+    t.lv[l].t_ab = l < scale ? th[3 * l + 1] : 0u;
+    t.lv[l].t_abc = l < scale ? th[3 * l + 2] : 0u;
+  }
+  const gg_perm perm = gg_perm_make(1ULL << scale, seed);
+  kronecker_levels_kernel<<<grid_for(n_edges), 256, 0, stream>>>(t, scale, gg_stream_seed(seed, GG_STREAM_EDGES),
+                                                                 perm, permute, n_edges, src, dst);
   return (int)cudaGetLastError();
 }
 

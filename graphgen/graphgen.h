@@ -8,7 +8,9 @@
  * Workloads follow the paper's synthetic graphs (Sec. 5.1): Graph500
  * Stochastic Kronecker graphs with generator matrix [a b; c d] =
  * [0.57 0.19; 0.19 0.05], edge factor 16, vertex ids randomly permuted.
- * The paper's optional SKG noise is not applied here.
+ * The paper's SKG noise (parameter 0.1 in Sec. 5.1) is available through
+ * per-level thresholds (gg_rmat_edge_levels), built on the host by
+ * graphgen_rmat_noisy_levels in gen_host.c.
  *
  * Randomness: SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom
  * number generators", OOPSLA 2014) used as a counter-based generator: the
@@ -60,6 +62,7 @@ GG_FN uint64_t gg_draw(uint64_t s, uint64_t i) { return gg_mix64(s + (i + 1ULL) 
 #define GG_STREAM_EDGES 0u
 #define GG_STREAM_PERM 1u
 #define GG_STREAM_CHUNGLU 2u
+#define GG_STREAM_NOISE 3u
 GG_FN uint64_t gg_stream_seed(uint64_t seed, uint32_t stream) { return gg_draw(seed, stream); }
 
 /* Number of bits needed to hold ids in [0, n): smallest b with 2^b >= n (b >= 1). */
@@ -137,6 +140,25 @@ GG_FN void gg_rmat_edge(const gg_rmat_thresholds* th, uint32_t scale, uint64_t e
     } else {
       bu = 1; bv = 1;
     }
+    u = (u << 1) | bu;
+    v = (v << 1) | bv;
+  }
+  *u_out = u;
+  *v_out = v;
+}
+
+/* Same draws as gg_rmat_edge, with level l compared against th[l] (noisy SKG:
+ * one generator matrix per level). */
+GG_FN void gg_rmat_edge_levels(const gg_rmat_thresholds* th, uint32_t scale, uint64_t edge_seed, uint64_t e,
+                               uint64_t* u_out, uint64_t* v_out) {
+  const uint64_t per_edge = (scale + 1u) / 2u;
+  uint64_t u = 0, v = 0, w64 = 0;
+  for (uint32_t l = 0; l < scale; ++l) {
+    if ((l & 1u) == 0u) w64 = gg_draw(edge_seed, e * per_edge + (l >> 1));
+    const uint32_t w = (l & 1u) ? (uint32_t)(w64 >> 32) : (uint32_t)w64;
+    const gg_rmat_thresholds t = th[l];
+    const uint64_t bu = w >= t.t_ab ? 1u : 0u;
+    const uint64_t bv = (w >= t.t_a && w < t.t_ab) || w >= t.t_abc ? 1u : 0u;
     u = (u << 1) | bu;
     v = (v << 1) | bv;
   }
