@@ -67,8 +67,8 @@ WEDGE_API uint32_t wedge_version(void);
 /* sizeof of the ABI structs, for bindings to check their layouts: fills up to
  * cap of [graph_info, bins_info, sample_params, record, counts, estimates,
  * kernel_stat, request, launch_config, server_config, server_request,
- * request_timing, server_metrics, triangle_box, triangle_summary] and
- * returns 15. */
+ * request_timing, server_metrics, triangle_box, triangle_summary,
+ * exact_counts] and returns 16. */
 WEDGE_API int wedge_abi_sizes(uint64_t* sizes, int cap);
 
 /* --------------------------------------------------------------------------
@@ -419,6 +419,34 @@ WEDGE_API wedge_status wedge_estimate(const wedge_counts* c, double delta, wedge
  * ------------------------------------------------------------------------ */
 WEDGE_API wedge_status wedge_classify(const wedge_graph* g, const wedge_bins* b, int64_t n_wedges, const int32_t* v0,
                             const int32_t* v1, const int32_t* v2, uint8_t* q, wedge_stream s);
+
+/* --------------------------------------------------------------------------
+ * Exact counts (Sec. 2.1, 2.2): the quantities the sampler estimates, by
+ * enumerating every triangle once on the device (each edge oriented from
+ * the smaller to the larger (degree, id); the oriented rows of an edge's two
+ * endpoints are intersected). For every bin b: p_b (wedges centred in b) and
+ * pbq[b][q], the closed wedges centred in b whose two endpoints include
+ * q - 1 vertices of b (q = 1, 2, 3; Alg. Phase 4c's classes), with
+ * pbq[b][0] = p_b - pbq[b][1] - pbq[b][2] - pbq[b][3] (open wedges). Then
+ * c_b = (pbq[b][1] + pbq[b][2] + pbq[b][3]) / p_b, t = triangles and the
+ * global c = 3t/p (Eq. (CC)).
+ *   t_i: optional device uint64[n_vertices] receiving the closed wedges
+ *     centred at each vertex (triangles at i); NULL skips them.
+ *   Synchronises s. Needs about 4m + 12n bytes of device memory beyond the
+ *   graph (m undirected edges).
+ *   Errors: EINVAL for NULL handles or bins of another graph; ENOMEM;
+ *   ECUDA; ETIMEOUT (a bounded look-back wait gave up).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  uint64_t triangles;
+  uint32_t n_bins;
+  uint64_t p_total;
+  uint64_t p_b[WEDGE_MAX_BINS];
+  uint64_t pbq[WEDGE_MAX_BINS][4];
+} wedge_exact_counts;
+
+WEDGE_API wedge_status wedge_exact(const wedge_graph* g, const wedge_bins* b, uint64_t* t_i, wedge_stream s,
+                                   wedge_exact_counts* out);
 
 /* --------------------------------------------------------------------------
  * Triangle statistics from sampled wedges (Sec. 5.7, Thm 3.4).

@@ -149,8 +149,14 @@ class TriangleSummary(ctypes.Structure):
                 ("ratio_q", ctypes.c_double * 5), ("hist", (ctypes.c_uint64 * STAT_BINS) * STAT_BINS)]
 
 
+class ExactCounts(ctypes.Structure):
+    _fields_ = [("triangles", ctypes.c_uint64), ("n_bins", ctypes.c_uint32), ("p_total", ctypes.c_uint64),
+                ("p_b", ctypes.c_uint64 * MAX_BINS), ("pbq", (ctypes.c_uint64 * 4) * MAX_BINS)]
+
+
 _STRUCTS = [GraphInfo, BinsInfo, SampleParams, Record, CountsStruct, EstimatesStruct, KernelStat, Request,
-            LaunchConfig, ServerConfig, ServerRequest, RequestTiming, ServerMetrics, TriangleBox, TriangleSummary]
+            LaunchConfig, ServerConfig, ServerRequest, RequestTiming, ServerMetrics, TriangleBox, TriangleSummary,
+            ExactCounts]
 
 # Every symbol include/wedge.h declares.
 EXPORTS = ["wedge_status_str", "wedge_last_error", "wedge_version", "wedge_abi_sizes", "wedge_graph_build",
@@ -160,7 +166,8 @@ EXPORTS = ["wedge_status_str", "wedge_last_error", "wedge_version", "wedge_abi_s
            "wedge_degree_offsets_noalloc", "wedge_batch_create", "wedge_batch_launch", "wedge_batch_results",
            "wedge_batch_free", "wedge_batch_info", "wedge_sample_batch", "wedge_autotune", "wedge_server_create",
            "wedge_server_destroy", "wedge_server_add_graph", "wedge_server_remove_graph", "wedge_server_submit",
-           "wedge_server_wait", "wedge_server_stats", "wedge_probe_random_read", "wedge_triangle_stats"]
+           "wedge_server_wait", "wedge_server_stats", "wedge_probe_random_read", "wedge_triangle_stats",
+           "wedge_exact"]
 
 _lib = None
 
@@ -218,6 +225,7 @@ def load():
         "wedge_server_stats": ([P, P, ctypes.c_int], st),
         "wedge_probe_random_read": ([u64, u64, P, P], st),
         "wedge_triangle_stats": ([P, P, u64, u64, P, P, P], st),
+        "wedge_exact": ([P, P, P, P, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -434,6 +442,23 @@ def classify(graph: Graph, bins: Bins, v0, v1, v2, q, stream=None):
     pq, _ = _ptr(q, np.uint8)
     n = int(k0.shape[0])
     _check(lib.wedge_classify(graph.handle, bins.handle, n, p0, p1, p2, pq, _stream_handle(stream)))
+
+
+def exact(graph: Graph, bins: Bins, t_i=None, stream=None) -> dict:
+    """Exact triangle counts (wedge_exact): t, p_b, pbq[n_bins, 4] (q = 0 open,
+    1..3 closed by class); t_i: optional device uint64 tensor of n_vertices."""
+    lib = load()
+    out = ExactCounts()
+    pt = 0
+    if t_i is not None:
+        pt, arr = _ptr(t_i)
+        if int(np.prod(arr.shape)) < graph.info().n_vertices:
+            raise ValueError("t_i needs n_vertices entries")
+    _check(lib.wedge_exact(graph.handle, bins.handle, pt, _stream_handle(stream), ctypes.byref(out)))
+    nb = out.n_bins
+    pbq = np.array([list(out.pbq[i]) for i in range(nb)], np.uint64).reshape(nb, 4)
+    return {"triangles": int(out.triangles), "p_total": int(out.p_total), "p_b": np.array(out.p_b[:nb], np.uint64),
+            "pbq": pbq}
 
 
 BOX_FIELDS = ("count", "min", "q1", "median", "q3", "max", "whisker_lo", "whisker_hi", "outliers")

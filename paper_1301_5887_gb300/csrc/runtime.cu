@@ -214,13 +214,14 @@ const char* wedge_last_error(void) { return g_err; }
 uint32_t wedge_version(void) { return 0x000100u; }
 
 int wedge_abi_sizes(uint64_t* sizes, int cap) {
-  const uint64_t v[15] = {sizeof(wedge_graph_info),    sizeof(wedge_bins_info),      sizeof(wedge_sample_params),
+  const uint64_t v[16] = {sizeof(wedge_graph_info),    sizeof(wedge_bins_info),      sizeof(wedge_sample_params),
                           sizeof(wedge_record),        sizeof(wedge_counts),         sizeof(wedge_estimates),
                           sizeof(wedge_kernel_stat),   sizeof(wedge_request),        sizeof(wedge_launch_config),
                           sizeof(wedge_server_config), sizeof(wedge_server_request), sizeof(wedge_request_timing),
-                          sizeof(wedge_server_metrics), sizeof(wedge_triangle_box),  sizeof(wedge_triangle_summary)};
-  for (int i = 0; i < 15 && i < cap && sizes; ++i) sizes[i] = v[i];
-  return 15;
+                          sizeof(wedge_server_metrics), sizeof(wedge_triangle_box),  sizeof(wedge_triangle_summary),
+                          sizeof(wedge_exact_counts)};
+  for (int i = 0; i < 16 && i < cap && sizes; ++i) sizes[i] = v[i];
+  return 16;
 }
 
 const char* wedge_status_str(wedge_status st) {
