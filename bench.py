@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--no-rounding", action="store_true", help="skip the Phase 2a rounding-variant leg")
+    ap.add_argument("--no-rounding", action="store_true",
+                    help="skip the per-bin variant legs (Phase 2a rounding, sorted closure)")
     ap.add_argument("--tri-k", type=int, default=5_000_000,
                     help="samples of the triangle-statistics leg (Sec. 5.7 single-bin run; 0 skips it)")
     ap.add_argument("--serve-requests", type=int, default=2000,
@@ -487,6 +488,32 @@ def bench_rounding(wedge, graphgen, torch, g, b, iid_sampling_ms, reps=3, var_sc
                     "iid_sampling_ms_same_budget includes the global stream's K samples as well"}
 
 
+def bench_sorted_closure(wedge, g, b, reps=3):
+    """Per-bin sampling with closure checked in sorted order against the inline
+    check, same samples (identical counts), at the bench budget and 8x it."""
+    import numpy as np
+    out = []
+    for mult in (1, 8):
+        k = K_SAMPLES * mult
+        row = {"k_per_bin": k}
+        for name, flags in (("inline", wedge.FLAG_NO_GLOBAL),
+                            ("sorted", wedge.FLAG_SORTED_CLOSURE | wedge.FLAG_NO_GLOBAL)):
+            c = wedge.sample(g, b, seed=SEED, k_per_bin=k, flags=flags)
+            wedge.profile_reset()
+            wedge.profile_enable(True)
+            for r in range(reps):
+                c = wedge.sample(g, b, seed=SEED, k_per_bin=k, flags=flags)
+            wedge.profile_enable(False)
+            prof = wedge.profile_read()
+            ms = sum(v["total_ms"] for v in prof.values()) / reps
+            row[name] = {"ms": ms, "kernels_ms": {kk: v["total_ms"] / reps for kk, v in prof.items()},
+                         "gwedges_per_s": int(c.k_b.sum()) / (ms / 1e3) / 1e9}
+            row[name + "_counts"] = c.counts_matrix()
+        row["identical"] = bool(np.array_equal(row.pop("inline_counts"), row.pop("sorted_counts")))
+        out.append(row)
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -612,11 +639,13 @@ def run_ours(args):
     # summarised per BinId(d_min); the call synchronises, so host time is device time.
     tri = None
     rounding = None
+    sorted_cl = None
     if args.tri_k > 0 or not args.no_rounding:
         g = wedge.graph_build(src, dst, n)
         b = wedge.bin(g, tau=TAU, omega=OMEGA)
     if not args.no_rounding:
         rounding = bench_rounding(wedge, graphgen, torch, g, b, samp_ms)
+        sorted_cl = bench_sorted_closure(wedge, g, b)
     if args.tri_k > 0:
         wedge.triangle_stats(g, b, SEED, args.tri_k)
         times = []
@@ -698,7 +727,7 @@ def run_ours(args):
                            "l2": f"inputs {8 * n_edges / 1e9:.1f} GB > 129 MB L2, no flush needed",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "gwedges_checked_per_s": gwps, "sampling_ms": samp_ms, "batched": batched, "serving": serving,
-                "triangle_stats": tri, "rounding": rounding, "roofline": roofline, "sampling_roofline": sampling_roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
+                "triangle_stats": tri, "rounding": rounding, "sorted_closure": sorted_cl, "roofline": roofline, "sampling_roofline": sampling_roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
                 "clocks": clk, "kernels": kernels,
                 "estimates": {"c_hat": info["c_hat"], "c_hat_global": info["c_hat_global"]}}
         print(json.dumps(line), flush=True)

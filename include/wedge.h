@@ -192,14 +192,26 @@ WEDGE_API wedge_status wedge_bins_copy(const wedge_bins* b, int32_t* L, uint64_t
  * is Alg. Phase 4c's and counts.k_b is the bin's realised total sum_v q_v,
  * the divisor of Alg. Phase 4c. The global stream is unchanged.
  *
+ *
+ * WEDGE_FLAG_SORTED_CLOSURE keeps the per-bin samples (same counters, same
+ * wedges, identical counts) but checks closure the way Alg. Phase 3b joins
+ * wedges with the edge list: every sample's closure query, packed with its
+ * stream and class as x << (b + P) | y << P | payload (x the endpoint with
+ * the smaller (degree, id), b = id bits, P = 2 + bits of the stream count),
+ * is radix-sorted, and the sorted queries are checked in order, each
+ * adjacency row searched once per run of queries. Needs 2b + P <= 64.
+ *
  * Errors: EINVAL if eps or delta is outside (0,1) while a budget is 0,
- * bins do not belong to g, records is set with WEDGE_FLAG_NO_GLOBAL, or
- * WEDGE_FLAG_ROUNDING is combined with first_sample != 0; ECUDA; ENOMEM;
- * ETIMEOUT (rounding: a scan look-back wait gave up).
+ * bins do not belong to g, records is set with WEDGE_FLAG_NO_GLOBAL,
+ * WEDGE_FLAG_ROUNDING is combined with first_sample != 0 or with
+ * WEDGE_FLAG_SORTED_CLOSURE, or a sorted-closure key would need more than 64
+ * bits; ECUDA; ENOMEM; ETIMEOUT (the variants: a scan or sort look-back wait
+ * gave up).
  * ------------------------------------------------------------------------ */
 #define WEDGE_FLAG_NO_GLOBAL 0x1u  /* skip the global stream */
 #define WEDGE_FLAG_NO_BINS 0x2u    /* skip the per-bin streams */
 #define WEDGE_FLAG_ROUNDING 0x4u   /* per-bin samples allocated per vertex (Alg. Phase 2a) */
+#define WEDGE_FLAG_SORTED_CLOSURE 0x8u  /* per-bin closure queries sorted, then checked in order */
 
 typedef struct {
   uint64_t seed;

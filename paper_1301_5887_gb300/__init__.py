@@ -31,6 +31,7 @@ STAT_BINS = 34
 FLAG_NO_GLOBAL = 0x1
 FLAG_NO_BINS = 0x2
 FLAG_ROUNDING = 0x4  # per-bin samples allocated per vertex by probabilistic rounding (Alg. Phase 2a)
+FLAG_SORTED_CLOSURE = 0x8  # per-bin closure queries radix-sorted, then checked in order (Alg. Phase 3b join)
 
 STATUS = {0: "WEDGE_OK", 1: "WEDGE_EINVAL", 2: "WEDGE_ENOMEM", 3: "WEDGE_ECUDA", 4: "WEDGE_ETIMEOUT",
           5: "WEDGE_EOVERFLOW"}

@@ -286,8 +286,8 @@ extern "C" wedge_status wedge_batch_create(const wedge_request* reqs, int n_reqs
     if (q.bins->graph_uid != q.graph->uid)
       return bail(fail(WEDGE_EINVAL, "wedge_batch_create: request %d: bins were built from another graph", r));
     const wedge_sample_params& sp = q.params;
-    if ((sp.flags & WEDGE_FLAG_ROUNDING) && !(sp.flags & WEDGE_FLAG_NO_BINS))
-      return bail(fail(WEDGE_EINVAL, "wedge_batch_create: request %d: WEDGE_FLAG_ROUNDING runs through wedge_sample only", r));
+    if ((sp.flags & (WEDGE_FLAG_ROUNDING | WEDGE_FLAG_SORTED_CLOSURE)) && !(sp.flags & WEDGE_FLAG_NO_BINS))
+      return bail(fail(WEDGE_EINVAL, "wedge_batch_create: request %d: the per-bin variants run through wedge_sample only", r));
     const bool want_bins = !(sp.flags & WEDGE_FLAG_NO_BINS);
     const bool want_glob = !(sp.flags & WEDGE_FLAG_NO_GLOBAL);
     uint64_t k_bin = sp.k_per_bin, k_glob = sp.k_global;

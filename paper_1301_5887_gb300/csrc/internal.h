@@ -62,6 +62,11 @@ wedge_status scan_u64_with_total(const uint64_t* in, uint64_t* out, int64_t n, v
 wedge_status sample_rounding(const wedge_graph* g, const wedge_bins* b, uint64_t seed, const uint64_t* k_of_bin,
                              cudaStream_t s, wedge_counts* out);
 
+// Per-bin samples with closure checked in sorted order (sorted.cu); same
+// counts as the inline check. Fills out->k_b and out->q; synchronises s.
+wedge_status sample_sorted_closure(const wedge_graph* g, const wedge_bins* b, uint64_t seed, uint64_t first_sample,
+                                   const uint64_t* k_of_bin, cudaStream_t s, wedge_counts* out);
+
 uint64_t next_uid();
 
 }  // namespace wedge

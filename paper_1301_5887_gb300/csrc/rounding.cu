@@ -4,7 +4,8 @@
 //
 // 1. k_round_alloc: for each vertex v of L (degree d >= 2, bin b), the ideal
 //    share q* = C(d,2) k_b / p_b is split exactly into floor and remainder
-//    with 128-bit integer arithmetic; one Philox draw rounds it up with
+//    (a 64.64 fixed-point estimate, corrected with 128-bit products); one
+//    Philox draw rounds it up with
 //    probability (C(d,2) k_b mod p_b) / p_b, so E[q_v] = q*. q_v goes to q[j]
 //    at v's position j in L.
 // 2. an exclusive scan of q over L gives Q[j], the first sample index of the
@@ -38,7 +39,7 @@ struct AllocArgs {
   const int32_t* deg;
   int64_t n2;
   const uint64_t* lo;   // bin table (n_bins)
-  const uint64_t* kp;   // [2 * n_bins]: k_b then p_b
+  const uint64_t* kp;   // [4 * n_bins]: k_b, p_b, then F_b = floor(k_b 2^64 / p_b) as low and high words
   uint32_t nb, pow2;
   uint32_t seed_lo, seed_hi;
   uint64_t* q;          // n2 outputs
@@ -48,10 +49,14 @@ __global__ __launch_bounds__(ROUND_THREADS) void k_round_alloc(AllocArgs a) {
   __shared__ uint64_t s_lo[WEDGE_MAX_BINS];
   __shared__ uint64_t s_k[WEDGE_MAX_BINS];
   __shared__ uint64_t s_p[WEDGE_MAX_BINS];
+  __shared__ uint64_t s_flo[WEDGE_MAX_BINS];
+  __shared__ uint64_t s_fhi[WEDGE_MAX_BINS];
   for (int i = threadIdx.x; i < (int)a.nb; i += ROUND_THREADS) {
     s_lo[i] = a.lo[i];
     s_k[i] = a.kp[i];
     s_p[i] = a.kp[a.nb + i];
+    s_flo[i] = a.kp[2 * a.nb + i];
+    s_fhi[i] = a.kp[3 * a.nb + i];
   }
   __syncthreads();
   const BinTable bt{s_lo, a.nb, a.pow2};
@@ -63,11 +68,11 @@ __global__ __launch_bounds__(ROUND_THREADS) void k_round_alloc(AllocArgs a) {
     const uint64_t kb = s_k[b], pb = s_p[b];
     uint64_t q = 0;
     if (kb != 0) {
-      // floor(num / pb) from an FP64 estimate (q* <= kb <= 2^40, relative
-      // error a few 2^-53: off by at most 2), corrected exactly in 128 bits.
+      // floor(num / pb) from the bin's 64.64 fixed-point ratio F = floor(k_b 2^64 / p_b):
+      // floor(c F / 2^64) is floor(q*) or one less (c / 2^64 < 1); corrected exactly.
       const uint64_t c = d * (d - 1) / 2;
       const unsigned __int128 num = (unsigned __int128)c * kb;
-      uint64_t fl = (uint64_t)__dmul_rn(__ddiv_rn((double)c, (double)pb), (double)kb);
+      uint64_t fl = c * s_fhi[b] + __umul64hi(c, s_flo[b]);
       unsigned __int128 prod = (unsigned __int128)fl * pb;
       while (prod > num) {
         fl -= 1;
@@ -198,7 +203,7 @@ wedge_status sample_rounding(const wedge_graph* g, const wedge_bins* b, uint64_t
   }
   if (n2 == 0) return WEDGE_OK;
 
-  uint64_t* kp = nullptr;     // [2 nb]
+  uint64_t* kp = nullptr;     // [4 nb]
   uint64_t* q = nullptr;      // n2
   uint64_t* Q = nullptr;      // n2 + 1
   int64_t* d_start = nullptr; // nb + 1
@@ -220,7 +225,7 @@ wedge_status sample_rounding(const wedge_graph* g, const wedge_bins* b, uint64_t
     return st;
   };
   wedge_status st;
-  if ((st = dalloc_n(&kp, 2 * (size_t)nb, s, "wedge_sample")) != WEDGE_OK) return done(st);
+  if ((st = dalloc_n(&kp, 4 * (size_t)nb, s, "wedge_sample")) != WEDGE_OK) return done(st);
   if ((st = dalloc_n(&q, (size_t)n2, s, "wedge_sample")) != WEDGE_OK) return done(st);
   if ((st = dalloc_n(&Q, (size_t)n2 + 1, s, "wedge_sample")) != WEDGE_OK) return done(st);
   if ((st = dalloc_n(&d_start, (size_t)nb + 1, s, "wedge_sample")) != WEDGE_OK) return done(st);
@@ -228,10 +233,14 @@ wedge_status sample_rounding(const wedge_graph* g, const wedge_bins* b, uint64_t
   if ((st = dalloc(&scratch, scan_scratch_bytes(n2), s, "wedge_sample")) != WEDGE_OK) return done(st);
   if ((st = dalloc_n(&derr, 1, s, "wedge_sample")) != WEDGE_OK) return done(st);
 
-  std::vector<uint64_t> h_kp(2 * (size_t)nb);
+  std::vector<uint64_t> h_kp(4 * (size_t)nb);
   for (uint32_t k = 0; k < nb; ++k) {
-    h_kp[k] = inf.p_b[k] ? k_of_bin[k] : 0;
-    h_kp[nb + k] = inf.p_b[k] ? inf.p_b[k] : 1;
+    const uint64_t kb = inf.p_b[k] ? k_of_bin[k] : 0, pb = inf.p_b[k] ? inf.p_b[k] : 1;
+    const unsigned __int128 f = ((unsigned __int128)kb << 64) / pb;  // < 2^104 for k_b <= 2^40
+    h_kp[k] = kb;
+    h_kp[nb + k] = pb;
+    h_kp[2 * nb + k] = (uint64_t)f;
+    h_kp[3 * nb + k] = (uint64_t)(f >> 64);
   }
   cudaError_t e = cudaMemcpyAsync(kp, h_kp.data(), h_kp.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)

@@ -335,10 +335,15 @@ extern "C" wedge_status wedge_sample(const wedge_graph* g, const wedge_bins* b, 
                                      wedge_stream stream, wedge_counts* out) {
   clear_error();
   if (!g || !b || !sp || !out) return fail(WEDGE_EINVAL, "wedge_sample: NULL argument");
-  const bool rounding = (sp->flags & WEDGE_FLAG_ROUNDING) && !(sp->flags & WEDGE_FLAG_NO_BINS);
-  if (!rounding) return sample_streams(g, b, sp, stream, out);
-  // Alg. Phase 2a variant: the global stream as usual, then the bins by rounding.
-  if (sp->first_sample != 0) return fail(WEDGE_EINVAL, "wedge_sample: WEDGE_FLAG_ROUNDING needs first_sample = 0");
+  const bool bins = !(sp->flags & WEDGE_FLAG_NO_BINS);
+  const bool rounding = bins && (sp->flags & WEDGE_FLAG_ROUNDING);
+  const bool sorted = bins && (sp->flags & WEDGE_FLAG_SORTED_CLOSURE);
+  if (!rounding && !sorted) return sample_streams(g, b, sp, stream, out);
+  if (rounding && sorted)
+    return fail(WEDGE_EINVAL, "wedge_sample: WEDGE_FLAG_ROUNDING and WEDGE_FLAG_SORTED_CLOSURE exclude each other");
+  // Variants of the per-bin streams: the global stream as usual, then the bins.
+  if (rounding && sp->first_sample != 0)
+    return fail(WEDGE_EINVAL, "wedge_sample: WEDGE_FLAG_ROUNDING needs first_sample = 0");
   if (b->graph_uid != g->uid) return fail(WEDGE_EINVAL, "wedge_sample: bins were built from another graph");
   uint64_t k_bin = sp->k_per_bin;
   if (k_bin == 0 && !sp->k_bin) {
@@ -352,5 +357,7 @@ extern "C" wedge_status wedge_sample(const wedge_graph* g, const wedge_bins* b, 
   const uint32_t nb = b->info.n_bins;
   std::vector<uint64_t> k_of_bin(nb);
   for (uint32_t k = 0; k < nb; ++k) k_of_bin[k] = sp->k_bin ? sp->k_bin[k] : k_bin;
-  return sample_rounding(g, b, sp->seed, k_of_bin.data(), reinterpret_cast<cudaStream_t>(stream), out);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (rounding) return sample_rounding(g, b, sp->seed, k_of_bin.data(), s, out);
+  return sample_sorted_closure(g, b, sp->seed, sp->first_sample, k_of_bin.data(), s, out);
 }

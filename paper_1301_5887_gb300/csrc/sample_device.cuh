@@ -48,10 +48,11 @@ __device__ __forceinline__ bool closed_wedge(const int32_t* __restrict__ adj, in
   return row_contains(adj, o2, o2 + d2, v1);
 }
 
-// The wedge for random words r of a stream over L[start, start+len) with
-// wedge total p and prefix base wbase = W[start].
-__device__ __forceinline__ Wedge draw_wedge_thread(const GraphView& g, int64_t start, int64_t len, uint64_t p,
-                                                   uint64_t wbase, const Philox4& r) {
+// Centre and endpoints (no closure) for random words r of a stream over
+// L[start, start+len) with wedge total p and prefix base wbase = W[start];
+// fills everything but closed and returns the endpoints' row starts.
+__device__ __forceinline__ Wedge draw_pair_thread(const GraphView& g, int64_t start, int64_t len, uint64_t p,
+                                                  uint64_t wbase, const Philox4& r, int64_t& o1, int64_t& o2) {
   Wedge w;
   const uint64_t t = mulhi64((uint64_t)r.r0 | ((uint64_t)r.r1 << 32), p);
   const uint64_t T = wbase + t;
@@ -70,10 +71,19 @@ __device__ __forceinline__ Wedge draw_wedge_thread(const GraphView& g, int64_t s
   const uint64_t j = jp + (jp >= i ? 1ULL : 0ULL);
   w.v1 = __ldg(g.adj + o0 + (int64_t)i);
   w.v2 = __ldg(g.adj + o0 + (int64_t)j);
-  const int64_t o1 = __ldg(g.off + w.v1);
+  o1 = __ldg(g.off + w.v1);
   w.d1 = __ldg(g.off + w.v1 + 1) - o1;
-  const int64_t o2 = __ldg(g.off + w.v2);
+  o2 = __ldg(g.off + w.v2);
   w.d2 = __ldg(g.off + w.v2 + 1) - o2;
+  w.closed = false;
+  return w;
+}
+
+// The wedge for random words r, with its closure.
+__device__ __forceinline__ Wedge draw_wedge_thread(const GraphView& g, int64_t start, int64_t len, uint64_t p,
+                                                   uint64_t wbase, const Philox4& r) {
+  int64_t o1, o2;
+  Wedge w = draw_pair_thread(g, start, len, p, wbase, r, o1, o2);
   w.closed = closed_wedge(g.adj, w.v1, w.v2, o1, w.d1, o2, w.d2);
   return w;
 }

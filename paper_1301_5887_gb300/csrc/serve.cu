@@ -369,8 +369,8 @@ extern "C" wedge_status wedge_server_remove_graph(wedge_server* sv, uint64_t gra
 extern "C" wedge_status wedge_server_submit(wedge_server* sv, const wedge_server_request* req, uint64_t* ticket) {
   clear_error();
   if (!sv || !req || !ticket) return fail(WEDGE_EINVAL, "wedge_server_submit: NULL argument");
-  if ((req->flags & WEDGE_FLAG_ROUNDING) && !(req->flags & WEDGE_FLAG_NO_BINS))
-    return fail(WEDGE_EINVAL, "wedge_server_submit: WEDGE_FLAG_ROUNDING runs through wedge_sample only");
+  if ((req->flags & (WEDGE_FLAG_ROUNDING | WEDGE_FLAG_SORTED_CLOSURE)) && !(req->flags & WEDGE_FLAG_NO_BINS))
+    return fail(WEDGE_EINVAL, "wedge_server_submit: the per-bin variants run through wedge_sample only");
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     auto it = sv->graphs.find(req->graph_id);
