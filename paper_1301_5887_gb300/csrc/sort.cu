@@ -92,16 +92,51 @@ struct PassSmem {
 constexpr size_t PASS_SMEM = sizeof(PassSmem);
 
 // Peer mask of this lane's digit d (0..RADIX, RADIX = no key): the lanes of
-// the warp holding the same value, from one ballot per digit bit.
+// the warp holding the same value, from one ballot per digit bit (plus one
+// for the no-key marker unless every lane holds a key).
+template <bool FULL>
 __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
-  uint32_t peers = __ballot_sync(FULL_MASK, d >> RADIX_BITS);
-  if (!(d >> RADIX_BITS)) peers = ~peers;
+  uint32_t peers = FULL_MASK;
+  if (!FULL) {
+    peers = __ballot_sync(FULL_MASK, d >> RADIX_BITS);
+    if (!(d >> RADIX_BITS)) peers = ~peers;
+  }
 #pragma unroll
   for (int b = 0; b < RADIX_BITS; ++b) {
     const uint32_t m = __ballot_sync(FULL_MASK, (d >> b) & 1u);
     peers &= ((d >> b) & 1u) ? m : ~m;
   }
   return peers;
+}
+
+// Digit of a key: byte `sel` of its high (HI) or low 32-bit half (digits are
+// byte-aligned, so one never straddles the halves).
+template <bool HI>
+__device__ __forceinline__ uint32_t digit_of(uint64_t k, uint32_t sel) {
+  return __byte_perm(HI ? (uint32_t)(k >> 32) : (uint32_t)k, 0u, 0x4440u | sel);
+}
+
+// Stable warp-level rank of the tile's keys, scattered into shared memory in
+// digit order (FULL: every slot of the tile holds a key).
+template <bool HI, bool FULL>
+__device__ __forceinline__ void rank_and_place(PassSmem& sm, const uint64_t (&k)[SORT_ITEMS], uint32_t sel,
+                                               int nvalid, int warp, int lane) {
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < SORT_ITEMS; ++i) {
+    const int li = warp * (32 * SORT_ITEMS) + i * 32 + lane;
+    const uint32_t d = (FULL || li < nvalid) ? digit_of<HI>(k[i], sel) : (uint32_t)RADIX;
+    const uint32_t peers = digit_peers<FULL>(d);
+    const int leader = __ffs(peers) - 1;
+    uint32_t before = 0;
+    if (lane == leader && (FULL || d < (uint32_t)RADIX)) {
+      before = sm.whist[warp][d];
+      sm.whist[warp][d] = before + __popc(peers);
+    }
+    before = __shfl_sync(FULL_MASK, before, leader);
+    if (FULL || d < (uint32_t)RADIX) sm.keys[sm.dstart[d] + before + __popc(peers & lt)] = k[i];
+    __syncwarp();
+  }
 }
 
 // One LSD pass over a 4096-key tile:
@@ -113,10 +148,13 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
 //     by shuffle) and place them in shared memory in digit order;
 //  4. look back for the tile's global digit offsets;
 //  5. write runs of equal digits to their global positions.
+// HI: the pass's digit lies in the keys' high 32-bit half.
+template <bool HI>
 __global__ __launch_bounds__(SORT_THREADS) void k_sort_pass(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PassSmem& sm = *reinterpret_cast<PassSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t sel = (a.shift >> 3) & 3u;  // byte of the half
   if (tid == 0) sm.tile = atomicAdd(a.tile_ctr, 1u);
   for (int i = tid; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&sm.whist[0][0])[i] = 0;
   __syncthreads();
@@ -135,7 +173,7 @@ __global__ __launch_bounds__(SORT_THREADS) void k_sort_pass(PassArgs a) {
 #pragma unroll
   for (int i = 0; i < SORT_ITEMS; ++i) {
     const int li = warp * (32 * SORT_ITEMS) + i * 32 + lane;
-    if (li < nvalid) atomicAdd(&sm.whist[warp][(uint32_t)(k[i] >> a.shift) & (RADIX - 1)], 1u);
+    if (li < nvalid) atomicAdd(&sm.whist[warp][digit_of<HI>(k[i], sel)], 1u);
   }
   __syncthreads();
 
@@ -171,22 +209,8 @@ __global__ __launch_bounds__(SORT_THREADS) void k_sort_pass(PassArgs a) {
   __syncthreads();
 
   // 3. stable warp-level rank, scattered into shared memory in digit order
-  const uint32_t lt = lanemask_lt();
-#pragma unroll
-  for (int i = 0; i < SORT_ITEMS; ++i) {
-    const int li = warp * (32 * SORT_ITEMS) + i * 32 + lane;
-    const uint32_t d = li < nvalid ? ((uint32_t)(k[i] >> a.shift) & (RADIX - 1)) : (uint32_t)RADIX;
-    const uint32_t peers = digit_peers(d);
-    const int leader = __ffs(peers) - 1;
-    uint32_t before = 0;
-    if (lane == leader && d < (uint32_t)RADIX) {
-      before = sm.whist[warp][d];
-      sm.whist[warp][d] = before + __popc(peers);
-    }
-    before = __shfl_sync(FULL_MASK, before, leader);
-    if (d < (uint32_t)RADIX) sm.keys[sm.dstart[d] + before + __popc(peers & lt)] = k[i];
-    __syncwarp();
-  }
+  if (nvalid == SORT_TILE) rank_and_place<HI, true>(sm, k, sel, nvalid, warp, lane);
+  else rank_and_place<HI, false>(sm, k, sel, nvalid, warp, lane);
 
   // 4. look-back for the global offset of each digit
   __syncthreads();
@@ -211,8 +235,7 @@ __global__ __launch_bounds__(SORT_THREADS) void k_sort_pass(PassArgs a) {
     const int pos = i * SORT_THREADS + tid;
     if (pos < nvalid) {
       const uint64_t key = sm.keys[pos];
-      const uint32_t dd = (uint32_t)(key >> a.shift) & (RADIX - 1);
-      __stcs(a.out + (sm.goff[dd] + (uint64_t)pos), key);
+      __stcs(a.out + (sm.goff[digit_of<HI>(key, sel)] + (uint64_t)pos), key);
     }
   }
 }
@@ -265,7 +288,11 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
 
   static bool attr_set = false;
   if (!attr_set) {
-    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PASS_SMEM),
+    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)PASS_SMEM),
+                   "radix sort: shared memory");
+    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)PASS_SMEM),
                    "radix sort: shared memory");
     attr_set = true;
   }
@@ -282,8 +309,10 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
     a.status = status;
     a.tile_ctr = ctr + p;
     a.err = derr;
-    st = launch("sort_onesweep_pass", s,
-                [&] { k_sort_pass<<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a); });
+    st = launch("sort_onesweep_pass", s, [&] {
+      if (a.shift >= 32) k_sort_pass<true><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
+      else k_sort_pass<false><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
+    });
     if (st != WEDGE_OK) return st;
     uint64_t* t = src;
     src = dst;
