@@ -6,6 +6,8 @@
 //   1. expand: each input pair (u, v), u != v, emits (u,v) and (v,u); self-loops
 //      emit a sentinel that sorts last; ids outside [0, n) raise DERR_BAD_ID.
 //      The sort's digit histograms are accumulated here as the keys appear.
+//      A host edge list streams through two device staging slots, its
+//      transfer overlapping the expansion of the previous chunk.
 //   2. sort: LSD radix over the 2b significant bits.
 //   3. dedup: adjacent-unique keys become adjacency entries (low b bits);
 //      one atomic per run of equal sources per warp counts each row's
@@ -189,6 +191,59 @@ using namespace wedge;
     if (e__ != cudaSuccess) return bail(cuda_fail(e__, what)); \
   } while (0)
 
+// Edges per staging slot for host edge lists (two slots of two int32 arrays:
+// 512 MiB of device memory in all).
+constexpr int64_t STAGE_EDGES = int64_t(1) << 25;
+
+// Copy chunk after chunk of a host edge list into the two staging slots on a
+// side stream and expand each on s as soon as it has arrived; a slot is
+// refilled only after s has consumed its previous chunk.
+template <typename Expand>
+wedge_status stage_and_expand(const int32_t* src, const int32_t* dst, int64_t n_edges, int64_t chunk,
+                              int32_t* src_stage, int32_t* dst_stage, cudaStream_t s, Expand&& expand) {
+  cudaStream_t cs = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+  auto finish = [&](wedge_status st) {
+    // On failure s may not have waited for every copy: let them land before
+    // the caller frees the slots. Otherwise destroying a stream or event with
+    // work pending is deferred by CUDA until that work completes.
+    if (st != WEDGE_OK && cs) cudaStreamSynchronize(cs);
+    for (int i = 0; i < 2; ++i) {
+      if (copied[i]) cudaEventDestroy(copied[i]);
+      if (consumed[i]) cudaEventDestroy(consumed[i]);
+    }
+    if (cs) cudaStreamDestroy(cs);
+    return st;
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&consumed[i], cudaEventDisableTiming);
+  }
+  // the copy stream starts after everything already queued on s
+  if (e == cudaSuccess) e = cudaEventRecord(consumed[0], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, consumed[0], 0);
+  if (e != cudaSuccess) return finish(cuda_fail(e, "wedge_graph_build: staging"));
+  int64_t i = 0;
+  for (int64_t e0 = 0; e0 < n_edges; e0 += chunk, ++i) {
+    const int slot = (int)(i & 1);
+    const int64_t len = std::min(chunk, n_edges - e0);
+    int32_t* sd = src_stage + slot * chunk;
+    int32_t* dd = dst_stage + slot * chunk;
+    if (i >= 2) e = cudaStreamWaitEvent(cs, consumed[slot], 0);  // expansion of chunk i - 2 is done
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sd, src + e0, (size_t)len * 4, cudaMemcpyDefault, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dd, dst + e0, (size_t)len * 4, cudaMemcpyDefault, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(copied[slot], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, copied[slot], 0);
+    if (e != cudaSuccess) return finish(cuda_fail(e, "wedge_graph_build: staging"));
+    const wedge_status st = expand(sd, dd, e0, len);
+    if (st != WEDGE_OK) return finish(st);
+    e = cudaEventRecord(consumed[slot], s);
+    if (e != cudaSuccess) return finish(cuda_fail(e, "wedge_graph_build: staging"));
+  }
+  return finish(WEDGE_OK);
+}
+
 extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst, int64_t n_edges, int32_t n_vertices,
                                           wedge_stream stream, wedge_graph** out) {
   clear_error();
@@ -232,19 +287,6 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
   BUILD_TRY(cudaMemsetAsync(g->deg, 0, (size_t)n_vertices * sizeof(int32_t), s), "wedge_graph_build");
 
   if (n_edges > 0) {
-    const int32_t* s_in = src;
-    const int32_t* d_in = dst;
-    if (!device_accessible(src) || !device_accessible(dst)) {
-      // Host edge list: copy into device staging buffers on the caller's stream.
-      if ((st = dalloc_n(&bb.src_dev, (size_t)n_edges, s, "wedge_graph_build: staging")) != WEDGE_OK) return bail(st);
-      if ((st = dalloc_n(&bb.dst_dev, (size_t)n_edges, s, "wedge_graph_build: staging")) != WEDGE_OK) return bail(st);
-      cudaError_t e1 = cudaMemcpyAsync(bb.src_dev, src, (size_t)n_edges * 4, cudaMemcpyDefault, s);
-      cudaError_t e2 = cudaMemcpyAsync(bb.dst_dev, dst, (size_t)n_edges * 4, cudaMemcpyDefault, s);
-      if (e1 != cudaSuccess) return bail(cuda_fail(e1, "wedge_graph_build: copy src"));
-      if (e2 != cudaSuccess) return bail(cuda_fail(e2, "wedge_graph_build: copy dst"));
-      s_in = bb.src_dev;
-      d_in = bb.dst_dev;
-    }
     if ((st = dalloc_n(&bb.keys_a, (size_t)nkeys, s, "wedge_graph_build: keys")) != WEDGE_OK) return bail(st);
     if ((st = dalloc_n(&bb.keys_b, (size_t)nkeys, s, "wedge_graph_build: keys")) != WEDGE_OK) return bail(st);
     const size_t scratch_bytes =
@@ -254,16 +296,29 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
 
     const int passes = (2 * (int)b + 7) / 8;
     if ((st = sort_clear_hist(bb.scratch, s)) != WEDGE_OK) return bail(st);
-    st = launch("expand_edges", s, [&] {
-      k_expand<<<grid_stride_blocks(n_edges, 256), 256, 0, s>>>(s_in, d_in, n_edges, n_vertices, b, sentinel, passes,
-                                                                reinterpret_cast<ulonglong2*>(bb.keys_a),
-                                                                sort_hist_area(bb.scratch), bb.derr);
-    });
-    if (st != WEDGE_OK) return bail(st);
-    // Staging buffers are no longer needed once the keys exist.
-    dfree(bb.src_dev, s);
-    dfree(bb.dst_dev, s);
-    bb.src_dev = bb.dst_dev = nullptr;
+    ulonglong2* keys2 = reinterpret_cast<ulonglong2*>(bb.keys_a);
+    auto expand = [&](const int32_t* s_in, const int32_t* d_in, int64_t e0, int64_t len) {
+      return launch("expand_edges", s, [&] {
+        k_expand<<<grid_stride_blocks(len, 256), 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes,
+                                                              keys2 + e0, sort_hist_area(bb.scratch), bb.derr);
+      });
+    };
+    if (device_accessible(src) && device_accessible(dst)) {
+      if ((st = expand(src, dst, 0, n_edges)) != WEDGE_OK) return bail(st);
+    } else {
+      // Host edge list: stream it through two staging slots. A copy stream
+      // fills slot i % 2 with chunk i while the caller's stream expands chunk
+      // i - 1, so the transfer over the host link overlaps the expansion.
+      const int64_t chunk = std::min<int64_t>(n_edges, STAGE_EDGES);
+      if ((st = dalloc_n(&bb.src_dev, 2 * (size_t)chunk, s, "wedge_graph_build: staging")) != WEDGE_OK) return bail(st);
+      if ((st = dalloc_n(&bb.dst_dev, 2 * (size_t)chunk, s, "wedge_graph_build: staging")) != WEDGE_OK) return bail(st);
+      if ((st = stage_and_expand(src, dst, n_edges, chunk, bb.src_dev, bb.dst_dev, s, expand)) != WEDGE_OK)
+        return bail(st);
+      // The staging slots go back to the pool once the last expansion is done.
+      dfree(bb.src_dev, s);
+      dfree(bb.dst_dev, s);
+      bb.src_dev = bb.dst_dev = nullptr;
+    }
 
     uint64_t* sorted = nullptr;
     st = radix_sort_u64(bb.keys_a, bb.keys_b, nkeys, 2 * (int)b, bb.scratch, bb.derr, s, &sorted, true);

@@ -352,6 +352,22 @@ def test_maximum_vertex_ids():
     assert b.info().n_wedge_vertices == sum(1 for v in rows if len(rows[v]) >= 2)
 
 
+def test_host_input_streams_in_chunks():
+    """Host edge lists larger than one staging slot (2^25 edges) stream through
+    two slots; pinned and pageable host input give the device-input CSR bit for bit."""
+    n = 1 << 22
+    hs, hd = graphgen.kronecker_host(22, n_edges=80_000_001, seed=5)  # 2 full chunks and a ragged one
+    ref = wedge.graph_build(torch.as_tensor(hs).cuda(), torch.as_tensor(hd).cuda(), n).csr_numpy()
+    for src, dst in ((hs, hd), (torch.as_tensor(hs).pin_memory(), torch.as_tensor(hd).pin_memory())):
+        got = wedge.graph_build(src, dst, n).csr_numpy()
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+    wedge.profile_reset()
+    wedge.profile_enable(False)
+    wedge.graph_build(hs, hd, n)
+    assert wedge.profile_read()["expand_edges"]["launches"] == 3
+
+
 def test_profile_counts_launches():
     wedge.profile_reset()
     wedge.profile_enable(True)
