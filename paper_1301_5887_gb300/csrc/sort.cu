@@ -92,21 +92,19 @@ struct PassSmem {
 constexpr size_t PASS_SMEM = sizeof(PassSmem);
 
 // Peer mask of this lane's digit d (0..RADIX, RADIX = no key): the lanes of
-// the warp holding the same value, from one ballot per digit bit (plus one
-// for the no-key marker unless every lane holds a key).
+// the warp holding the same value. One ballot per digit bit (plus one for the
+// no-key marker unless every lane holds a key), all issued first; a lane
+// differs from this one where a ballot disagrees with this lane's bit.
 template <bool FULL>
 __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
-  uint32_t peers = FULL_MASK;
-  if (!FULL) {
-    peers = __ballot_sync(FULL_MASK, d >> RADIX_BITS);
-    if (!(d >> RADIX_BITS)) peers = ~peers;
-  }
+  uint32_t m[RADIX_BITS];
 #pragma unroll
-  for (int b = 0; b < RADIX_BITS; ++b) {
-    const uint32_t m = __ballot_sync(FULL_MASK, (d >> b) & 1u);
-    peers &= ((d >> b) & 1u) ? m : ~m;
-  }
-  return peers;
+  for (int b = 0; b < RADIX_BITS; ++b) m[b] = __ballot_sync(FULL_MASK, (d >> b) & 1u);
+  uint32_t differ = 0;
+#pragma unroll
+  for (int b = 0; b < RADIX_BITS; ++b) differ |= m[b] ^ (0u - ((d >> b) & 1u));
+  if (!FULL) differ |= __ballot_sync(FULL_MASK, d >> RADIX_BITS) ^ (0u - (d >> RADIX_BITS));
+  return ~differ;
 }
 
 // Digit of a key: byte `sel` of its high (HI) or low 32-bit half (digits are
@@ -117,7 +115,10 @@ __device__ __forceinline__ uint32_t digit_of(uint64_t k, uint32_t sel) {
 }
 
 // Stable warp-level rank of the tile's keys, scattered into shared memory in
-// digit order (FULL: every slot of the tile holds a key).
+// digit order (FULL: every slot of the tile holds a key). whist[warp][d] holds
+// the tile position of this warp's next key of digit d: every peer reads it,
+// the lowest peer advances it past the group, and each key lands at that
+// position plus the number of its peers in lower lanes.
 template <bool HI, bool FULL>
 __device__ __forceinline__ void rank_and_place(PassSmem& sm, const uint64_t (&k)[SORT_ITEMS], uint32_t sel,
                                                int nvalid, int warp, int lane) {
@@ -125,16 +126,16 @@ __device__ __forceinline__ void rank_and_place(PassSmem& sm, const uint64_t (&k)
 #pragma unroll
   for (int i = 0; i < SORT_ITEMS; ++i) {
     const int li = warp * (32 * SORT_ITEMS) + i * 32 + lane;
-    const uint32_t d = (FULL || li < nvalid) ? digit_of<HI>(k[i], sel) : (uint32_t)RADIX;
+    const bool has = FULL || li < nvalid;
+    const uint32_t d = has ? digit_of<HI>(k[i], sel) : (uint32_t)RADIX;
     const uint32_t peers = digit_peers<FULL>(d);
-    const int leader = __ffs(peers) - 1;
-    uint32_t before = 0;
-    if (lane == leader && (FULL || d < (uint32_t)RADIX)) {
-      before = sm.whist[warp][d];
-      sm.whist[warp][d] = before + __popc(peers);
+    const uint32_t below = peers & lt;
+    const uint32_t next = has ? sm.whist[warp][d] : 0u;
+    __syncwarp();  // every peer has read the counter before the lowest one moves it
+    if (has) {
+      if (below == 0) sm.whist[warp][d] = next + __popc(peers);
+      sm.keys[next + __popc(below)] = k[i];
     }
-    before = __shfl_sync(FULL_MASK, before, leader);
-    if (FULL || d < (uint32_t)RADIX) sm.keys[sm.dstart[d] + before + __popc(peers & lt)] = k[i];
     __syncwarp();
   }
 }
@@ -143,9 +144,9 @@ __device__ __forceinline__ void rank_and_place(PassSmem& sm, const uint64_t (&k)
 //  1. load 16 keys per thread (coalesced) and count digits per warp;
 //  2. publish the tile's digit counts to the look-back words at once, so
 //     later tiles need not wait for this tile's ranking;
-//  3. rank keys stably within each warp (ballot-built peer masks; the
-//     lowest peer bumps the warp's digit counter and shares the old value
-//     by shuffle) and place them in shared memory in digit order;
+//  3. rank keys stably within each warp (ballot-built peer masks; every
+//     peer reads the warp's position counter for its digit, the lowest peer
+//     advances it) and place them in shared memory in digit order;
 //  4. look back for the tile's global digit offsets;
 //  5. write runs of equal digits to their global positions.
 // HI: the pass's digit lies in the keys' high 32-bit half.
@@ -205,6 +206,9 @@ __global__ __launch_bounds__(SORT_THREADS) void k_sort_pass(PassArgs a) {
     for (int w = 0; w < RADIX / 32; ++w)
       if (w < warp) pre += sm.wsum[w];
     sm.dstart[tid] = pre + cnt;
+    // per-warp counters become tile positions: digit start + earlier warps' keys
+#pragma unroll
+    for (int w = 0; w < SORT_WARPS; ++w) sm.whist[w][tid] += pre + cnt;
   }
   __syncthreads();
 
