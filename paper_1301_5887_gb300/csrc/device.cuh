@@ -66,6 +66,54 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t* status, int64_t til
   return excl;
 }
 
+// Warp-wide look-back over status words of stride 1 (call with all 32 lanes
+// of one warp). The nearest predecessor is polled alone; once it holds only
+// an aggregate, the lanes read 32 predecessors at once, so a chain of tiles
+// that have only published aggregates costs one round trip per 32 tiles
+// instead of one per tile. Same result on every lane. Bounded like lookback().
+__device__ __forceinline__ uint64_t lookback_warp(const uint64_t* status, int64_t tile, uint32_t epoch, uint32_t* err,
+                                                  int lane) {
+  uint64_t excl = 0;
+  int64_t hi = tile - 1;  // nearest predecessor not yet summed
+  uint32_t spins = 0;
+  int width = 1;          // lanes that read this round
+  while (hi >= 0) {
+    const int64_t j = hi - lane;
+    uint64_t w = 0;
+    bool ready = lane >= width ? false : true, inc = false;
+    if (lane < width && j >= 0) {
+      w = ld_relaxed(status + j);
+      const uint64_t flag = (w >> 58) & 3ULL;
+      ready = (uint32_t)(w >> 60) == epoch && flag != 0ULL;
+      inc = ready && flag == LB_INC;
+    }
+    const uint32_t incs = __ballot_sync(FULL_MASK, inc);
+    const uint32_t waits = __ballot_sync(FULL_MASK, !ready);
+    const int first_inc = incs ? __ffs(incs) - 1 : 32;
+    const int first_wait = waits ? __ffs(waits) - 1 : 32;
+    // lanes [0, take) are summed: every aggregate up to the nearest inclusive
+    // prefix, or up to the first predecessor that has not published yet
+    const int take = first_wait <= first_inc ? first_wait : first_inc + 1;
+    uint64_t v = lane < take ? (w & LB_VALUE_MASK) : 0ULL;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    excl += v;
+    if (first_inc < first_wait) break;  // reached an inclusive prefix
+    hi -= take;
+    if (take == 0) {
+      if (++spins >= SPIN_LIMIT) {
+        if (lane == 0) atomicOr(err, DERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(spins < 64 ? 32 : 256);
+      width = 1;
+    } else {
+      width = 32;
+    }
+  }
+  return excl;
+}
+
 // --------------------------------------------------------------------------
 // Arithmetic
 // --------------------------------------------------------------------------

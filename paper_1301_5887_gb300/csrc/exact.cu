@@ -111,17 +111,17 @@ __global__ __launch_bounds__(OR_THREADS) void k_orient(OrientArgs a) {
     if (w < warp) wpre += s_wsum[w];
     tile_total += s_wsum[w];
   }
-  if (tid == 0) {
+  if (warp == 0) {
     uint64_t* st = a.status + tile;
     uint64_t excl = 0;
     if (tile == 0) {
-      st_relaxed(st, lb_pack(1, LB_INC, tile_total));
+      if (lane == 0) st_relaxed(st, lb_pack(1, LB_INC, tile_total));
     } else {
-      st_relaxed(st, lb_pack(1, LB_AGG, tile_total));
-      excl = lookback(a.status, tile, 1, 1, a.err);
-      st_relaxed(st, lb_pack(1, LB_INC, excl + tile_total));
+      if (lane == 0) st_relaxed(st, lb_pack(1, LB_AGG, tile_total));
+      excl = lookback_warp(a.status, tile, 1, a.err, lane);
+      if (lane == 0) st_relaxed(st, lb_pack(1, LB_INC, excl + tile_total));
     }
-    s_excl = excl;
+    if (lane == 0) s_excl = excl;
   }
   __syncthreads();
   if (keep == 0) return;

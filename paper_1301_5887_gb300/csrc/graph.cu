@@ -105,7 +105,8 @@ __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restr
 
   // Row lengths first (they need no output position): sorted keys put equal
   // sources in consecutive lanes; the last lane of each run adds the run's
-  // unique keys to its row's degree. Meanwhile thread 0 looks back.
+  // unique keys to its row's degree. Then warp 0 looks back, 32 tiles at a
+  // time.
   const uint32_t lt = lanemask_lt();
   const uint32_t le = lt | (1u << lane);
 #pragma unroll
@@ -121,14 +122,16 @@ __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restr
       if (c) atomicAdd(deg + u, (int32_t)c);
     }
   }
-  if (tid == 0) {
+  if (warp == 0) {
     uint64_t excl = 0;
     if (tile != 0) {
-      excl = lookback(status, tile, 1, 1, err);
-      st_relaxed(st, lb_pack(1, LB_INC, excl + tile_total));
+      excl = lookback_warp(status, tile, 1, err, lane);
+      if (lane == 0) st_relaxed(st, lb_pack(1, LB_INC, excl + tile_total));
     }
-    s_excl = excl;
-    if ((tile + 1) * DEDUP_TILE >= nkeys) *n_unique = (int64_t)(excl + tile_total);
+    if (lane == 0) {
+      s_excl = excl;
+      if ((tile + 1) * DEDUP_TILE >= nkeys) *n_unique = (int64_t)(excl + tile_total);
+    }
   }
   __syncthreads();
   uint64_t pos = s_excl;
