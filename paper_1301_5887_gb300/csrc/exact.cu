@@ -53,6 +53,23 @@ __device__ __forceinline__ int32_t row_of(const int64_t* __restrict__ off, int32
   return lo;
 }
 
+// Row of entry e, given a row u with off[u] <= e: a few steps forward (the
+// common case), then a binary search, so long runs of empty rows cost
+// O(log n) instead of one step each.
+__device__ __forceinline__ int32_t next_row(const int64_t* __restrict__ off, int32_t n, int32_t u, int64_t e) {
+#pragma unroll 1
+  for (int t = 0; t < 4; ++t) {
+    if (e < __ldg(off + u + 1)) return u;
+    ++u;
+  }
+  int32_t lo = u, hi = n;  // off[lo] <= e < off[n]
+  while (hi - lo > 1) {
+    const int32_t mid = lo + ((hi - lo) >> 1);
+    if (__ldg(off + mid) <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 struct OrientArgs {
   const int64_t* off;
   const int32_t* adj;
@@ -86,8 +103,8 @@ __global__ __launch_bounds__(OR_THREADS) void k_orient(OrientArgs a) {
     for (int i = 0; i < OR_ITEMS; ++i) {
       const int64_t e = base + i;
       if (e >= a.n_adj) break;
-      while (e >= row_end) {
-        ++u;
+      if (e >= row_end) {
+        u = next_row(a.off, a.n, u, e);
         row_end = __ldg(a.off + u + 1);
         du = __ldg(a.deg + u);
       }
@@ -133,10 +150,10 @@ __global__ __launch_bounds__(OR_THREADS) void k_orient(OrientArgs a) {
   for (int i = 0; i < OR_ITEMS; ++i) {
     const int64_t e = base + i;
     if (e >= a.n_adj) break;
-    while (e >= row_end) {
+    if (e >= row_end) {
       if (run) atomicAdd(a.dplus + u, (int32_t)run);
       run = 0;
-      ++u;
+      u = next_row(a.off, a.n, u, e);
       row_end = __ldg(a.off + u + 1);
     }
     if (keep & (1u << i)) {

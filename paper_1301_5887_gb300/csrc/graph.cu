@@ -1,18 +1,27 @@
 // graph.cu — edge list -> CSR with degrees (wedge_graph_build).
 //
 // The paper's Phase 1a (Alg. Phase 1a) counts degrees by shuffling 2m
-// key-value pairs; here the same symmetrised pairs are packed into 64-bit keys
-// (u << b) | v, sorted by a device radix sort, deduplicated and cut into rows:
-//   1. expand: each input pair (u, v), u != v, emits (u,v) and (v,u); self-loops
-//      emit a sentinel that sorts last; ids outside [0, n) raise DERR_BAD_ID.
-//      The sort's digit histograms are accumulated here as the keys appear.
-//      A host edge list streams through two device staging slots, its
-//      transfer overlapping the expansion of the previous chunk.
+// key-value pairs. Here each undirected edge is sorted once, as the packed
+// key (min << b) | max; the other direction comes from the deduplicated
+// edges, whose transposed keys are already ordered by the smaller endpoint,
+// so a stable sort on the larger endpoint's bits alone orders them fully:
+//   1. expand: each input pair (u, v), u != v, emits (min << b) | max;
+//      self-loops emit a sentinel that sorts last; ids outside [0, n) raise
+//      DERR_BAD_ID. The sort's digit histograms are accumulated as the keys
+//      appear. A host edge list streams through two device staging slots,
+//      its transfer overlapping the expansion of the previous chunk.
 //   2. sort: LSD radix over the 2b significant bits.
-//   3. dedup: adjacent-unique keys become adjacency entries (low b bits);
-//      one atomic per run of equal sources per warp counts each row's
-//      length (the degree).
-//   4. offsets: exclusive scan of degrees into int64 row offsets.
+//   3. dedup: adjacent-unique keys (u, w), u < w, become the forward entries
+//      w of row u (compacted in order; one atomic per run of equal u per warp
+//      counts them) and the transposed keys (w << 32) | u, whose digit
+//      histograms are accumulated on the way.
+//   4. transposed sort: stable LSD radix over bits 32 .. 32 + b only (the
+//      input is already ordered by u), giving the backward entries u of each
+//      row w in ascending order; runs give the backward counts.
+//   5. rows: every backward entry of row x is below x and every forward one
+//      above, so row x is its backward entries followed by its forward ones;
+//      offsets are the sums of the two counts' exclusive scans, and each
+//      entry is written to its final position in one coalesced pass.
 #include <algorithm>
 #include <atomic>
 
@@ -27,11 +36,12 @@ constexpr int DEDUP_THREADS = 256;
 constexpr int DEDUP_ITEMS = 16;
 constexpr int DEDUP_TILE = DEDUP_THREADS * DEDUP_ITEMS;
 
-// Expand edges to packed keys and accumulate the radix sort's digit
-// histograms (8-bit digits, `passes` of them) in shared memory on the way.
+// Expand edges to packed keys (min << b) | max and accumulate the radix
+// sort's digit histograms (8-bit digits, `passes` of them) in shared memory
+// on the way.
 __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                                                 int64_t m, int32_t n, uint32_t b, uint64_t sentinel, int passes,
-                                                ulonglong2* __restrict__ keys, unsigned long long* __restrict__ hist,
+                                                uint64_t* __restrict__ keys, unsigned long long* __restrict__ hist,
                                                 uint32_t* err) {
   __shared__ uint32_t sh[SORT_MAX_PASSES * 256];
   for (int i = threadIdx.x; i < SORT_MAX_PASSES * 256; i += blockDim.x) sh[i] = 0;
@@ -39,37 +49,39 @@ __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src,
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
     const int32_t u = __ldcs(src + e), v = __ldcs(dst + e);
-    ulonglong2 kv;
+    uint64_t key;
     if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
       atomicOr(err, DERR_BAD_ID);
-      kv.x = kv.y = sentinel;
+      key = sentinel;
     } else if (u == v) {
-      kv.x = kv.y = sentinel;
+      key = sentinel;
     } else {
-      kv.x = ((uint64_t)u << b) | (uint64_t)v;
-      kv.y = ((uint64_t)v << b) | (uint64_t)u;
+      key = u < v ? ((uint64_t)u << b) | (uint64_t)v : ((uint64_t)v << b) | (uint64_t)u;
     }
-    __stcs(keys + e, kv);
-    for (int p = 0; p < passes; ++p) {
-      atomicAdd(&sh[p * 256 + (uint32_t)((kv.x >> (8 * p)) & 255u)], 1u);
-      atomicAdd(&sh[p * 256 + (uint32_t)((kv.y >> (8 * p)) & 255u)], 1u);
-    }
+    __stcs(keys + e, key);
+    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + (uint32_t)((key >> (8 * p)) & 255u)], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
     if (sh[i]) atomicAdd(&hist[i], (unsigned long long)sh[i]);
 }
 
-// Adjacent-unique of sorted keys -> adjacency entries and row lengths.
+// Adjacent-unique of sorted forward keys (u, w) -> unique forward keys (in
+// order), forward row lengths, and transposed keys (w << 32) | u with the
+// digit histograms of their `tpasses` low bytes of w.
 __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restrict__ keys, int64_t nkeys, uint32_t b,
-                                                         int32_t n, uint64_t sentinel, int32_t* __restrict__ adj,
-                                                         int32_t* __restrict__ deg, uint64_t* status,
+                                                         int32_t n, uint64_t sentinel, uint64_t* __restrict__ fwd,
+                                                         uint64_t* __restrict__ tkeys, int tpasses,
+                                                         unsigned long long* __restrict__ thist,
+                                                         int32_t* __restrict__ fdeg, uint64_t* status,
                                                          uint32_t* tile_ctr, uint32_t* err, int64_t* n_unique) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_wcount[DEDUP_THREADS / 32];
   __shared__ uint64_t s_excl;
+  __shared__ uint32_t s_hist[4 * 256];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  for (int i = tid; i < 4 * 256; i += DEDUP_THREADS) s_hist[i] = 0;
   __syncthreads();
   const int64_t tile = s_tile;
   const int64_t wbase = tile * DEDUP_TILE + warp * (32 * DEDUP_ITEMS);
@@ -103,10 +115,10 @@ __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restr
   uint64_t* st = status + tile;
   if (tid == 0) st_relaxed(st, lb_pack(1, tile == 0 ? LB_INC : LB_AGG, tile_total));  // publish early
 
-  // Row lengths first (they need no output position): sorted keys put equal
-  // sources in consecutive lanes; the last lane of each run adds the run's
-  // unique keys to its row's degree. Then warp 0 looks back, 32 tiles at a
-  // time.
+  // Row lengths and transposed-key histograms first (they need no output
+  // position): sorted keys put equal sources in consecutive lanes; the last
+  // lane of each run adds the run's unique keys to its row's forward count.
+  // Then warp 0 looks back, 32 tiles at a time.
   const uint32_t lt = lanemask_lt();
   const uint32_t le = lt | (1u << lane);
 #pragma unroll
@@ -119,7 +131,11 @@ __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restr
     if (run_end && u < (uint32_t)n) {
       const int start = 31 - __clz(starts & le);
       const uint32_t c = __popc(bal[i] & le & ~((1u << start) - 1u));
-      if (c) atomicAdd(deg + u, (int32_t)c);
+      if (c) atomicAdd(fdeg + u, (int32_t)c);
+    }
+    if ((bal[i] >> lane) & 1u) {
+      const uint32_t w = (uint32_t)(k[i] & vmask);
+      for (int p = 0; p < tpasses; ++p) atomicAdd(&s_hist[p * 256 + ((w >> (8 * p)) & 255u)], 1u);
     }
   }
   if (warp == 0) {
@@ -138,8 +154,79 @@ __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restr
   for (int w = 0; w < warp; ++w) pos += s_wcount[w];
 #pragma unroll
   for (int i = 0; i < DEDUP_ITEMS; ++i) {
-    if ((bal[i] >> lane) & 1u) adj[pos + __popc(bal[i] & lt)] = (int32_t)(k[i] & vmask);
+    if ((bal[i] >> lane) & 1u) {
+      const uint64_t at = pos + __popc(bal[i] & lt);
+      const uint32_t w = (uint32_t)(k[i] & vmask);
+      fwd[at] = k[i];
+      tkeys[at] = ((uint64_t)w << 32) | (k[i] >> b);
+    }
     pos += __popc(bal[i]);
+  }
+  for (int i = tid; i < tpasses * 256; i += DEDUP_THREADS)
+    if (s_hist[i]) atomicAdd(&thist[i], (unsigned long long)s_hist[i]);
+}
+
+// Backward row lengths: runs of equal w in the sorted transposed keys; the
+// last lane of each run within a warp's 32 keys adds the run to bdeg[w].
+__global__ __launch_bounds__(256) void k_count_back(const uint64_t* __restrict__ tkeys, int64_t m,
+                                                    int32_t* __restrict__ bdeg) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t le = lanemask_lt() | (1u << lane);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // whole warps step together, so the shuffles see every lane
+  const int64_t m_round = (m + 31) & ~int64_t(31);
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m_round; j += stride) {
+    const uint32_t w = j < m ? (uint32_t)(__ldcs(tkeys + j) >> 32) : 0xffffffffu;
+    const uint32_t w_prev = __shfl_up_sync(FULL_MASK, w, 1);
+    const uint32_t w_next = __shfl_down_sync(FULL_MASK, w, 1);
+    const uint32_t starts = __ballot_sync(FULL_MASK, lane == 0 || w_prev != w);
+    if (j < m && (lane == 31 || w_next != w)) {
+      const int start = 31 - __clz(starts & le);
+      atomicAdd(bdeg + w, lane - start + 1);
+    }
+  }
+}
+
+// Degrees, offsets (forward and backward exclusive scans added), largest degree.
+__global__ __launch_bounds__(256) void k_rows(const int32_t* __restrict__ fdeg, const int32_t* __restrict__ bdeg,
+                                              const int64_t* __restrict__ foff, const int64_t* __restrict__ boff,
+                                              int32_t n, int32_t* __restrict__ deg, int64_t* __restrict__ off,
+                                              int32_t* maxdeg) {
+  int32_t mx = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride) {
+    off[x] = foff[x] + boff[x];
+    if (x < n) {
+      const int32_t d = fdeg[x] + bdeg[x];
+      deg[x] = d;
+      mx = max(mx, d);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL_MASK, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(maxdeg, mx);
+}
+
+// Forward entry i, key (u << b) | w, goes to i + boff[u + 1]: row u starts at
+// foff[u] + boff[u] and holds its boff[u + 1] - boff[u] backward entries first.
+__global__ __launch_bounds__(256) void k_place_fwd(const uint64_t* __restrict__ fwd, int64_t m, uint32_t b,
+                                                   const int64_t* __restrict__ boff, int32_t* __restrict__ adj) {
+  const uint64_t vmask = (1ULL << b) - 1ULL;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const uint64_t key = __ldcs(fwd + i);
+    adj[i + __ldg(boff + (key >> b) + 1)] = (int32_t)(key & vmask);
+  }
+}
+
+// Backward entry j, key (w << 32) | u, goes to j + foff[w]: row w starts at
+// foff[w] + boff[w] and the backward entries of w are j - boff[w] into it.
+__global__ __launch_bounds__(256) void k_place_back(const uint64_t* __restrict__ tkeys, int64_t m,
+                                                    const int64_t* __restrict__ foff, int32_t* __restrict__ adj) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+    const uint64_t key = __ldcs(tkeys + j);
+    adj[j + __ldg(foff + (key >> 32))] = (int32_t)(uint32_t)key;
   }
 }
 
@@ -158,14 +245,20 @@ struct BuildBuffers {
   int32_t* dst_dev = nullptr;
   uint64_t* keys_a = nullptr;
   uint64_t* keys_b = nullptr;
+  uint64_t* fwd = nullptr;      // unique forward keys (u << b) | w
+  int32_t* fdeg = nullptr;      // forward then backward counts (2n)
+  int64_t* foff = nullptr;      // their exclusive scans (2(n + 1))
   void* scratch = nullptr;
   uint32_t* derr = nullptr;     // [0] error bits, then padding
-  int64_t* scalars = nullptr;   // [0] n_unique, [1] max degree (int32 in low half)
+  int64_t* scalars = nullptr;   // [0] unique undirected edges, [1] max degree (int32 in low half)
   ~BuildBuffers() {
     dfree(src_dev, s);
     dfree(dst_dev, s);
     dfree(keys_a, s);
     dfree(keys_b, s);
+    dfree(fwd, s);
+    dfree(fdeg, s);
+    dfree(foff, s);
     dfree(scratch, s);
     dfree(derr, s);
     dfree(scalars, s);
@@ -290,20 +383,30 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
   BUILD_TRY(cudaMemsetAsync(g->deg, 0, (size_t)n_vertices * sizeof(int32_t), s), "wedge_graph_build");
 
   if (n_edges > 0) {
-    if ((st = dalloc_n(&bb.keys_a, (size_t)nkeys, s, "wedge_graph_build: keys")) != WEDGE_OK) return bail(st);
-    if ((st = dalloc_n(&bb.keys_b, (size_t)nkeys, s, "wedge_graph_build: keys")) != WEDGE_OK) return bail(st);
+    // keys_a / keys_b: forward keys and their sort buffer, then the
+    // transposed keys and theirs; fwd: unique forward keys; fdeg/bdeg and
+    // foff/boff: forward and backward counts and their exclusive scans.
+    if ((st = dalloc_n(&bb.keys_a, (size_t)n_edges, s, "wedge_graph_build: keys")) != WEDGE_OK) return bail(st);
+    if ((st = dalloc_n(&bb.keys_b, (size_t)n_edges, s, "wedge_graph_build: keys")) != WEDGE_OK) return bail(st);
+    if ((st = dalloc_n(&bb.fwd, (size_t)n_edges, s, "wedge_graph_build: rows")) != WEDGE_OK) return bail(st);
+    if ((st = dalloc_n(&bb.fdeg, 2 * (size_t)n_vertices, s, "wedge_graph_build: rows")) != WEDGE_OK) return bail(st);
+    if ((st = dalloc_n(&bb.foff, 2 * ((size_t)n_vertices + 1), s, "wedge_graph_build: rows")) != WEDGE_OK)
+      return bail(st);
+    int32_t* bdeg = bb.fdeg + n_vertices;
+    int64_t* boff = bb.foff + (n_vertices + 1);
     const size_t scratch_bytes =
-        std::max(sort_scratch_bytes(nkeys, 2 * (int)b),
-                 std::max(scan_scratch_bytes(nkeys), scan_scratch_bytes(n_vertices)));
+        std::max(sort_scratch_bytes(n_edges, 2 * (int)b),
+                 std::max(scan_scratch_bytes(n_edges), scan_scratch_bytes(n_vertices)));
     if ((st = dalloc(&bb.scratch, scratch_bytes, s, "wedge_graph_build: scratch")) != WEDGE_OK) return bail(st);
+    BUILD_TRY(cudaMemsetAsync(bb.fdeg, 0, 2 * (size_t)n_vertices * sizeof(int32_t), s), "wedge_graph_build");
 
+    // 1. forward keys, with the forward sort's digit histograms
     const int passes = (2 * (int)b + 7) / 8;
     if ((st = sort_clear_hist(bb.scratch, s)) != WEDGE_OK) return bail(st);
-    ulonglong2* keys2 = reinterpret_cast<ulonglong2*>(bb.keys_a);
     auto expand = [&](const int32_t* s_in, const int32_t* d_in, int64_t e0, int64_t len) {
       return launch("expand_edges", s, [&] {
         k_expand<<<grid_stride_blocks(len, 256), 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes,
-                                                              keys2 + e0, sort_hist_area(bb.scratch), bb.derr);
+                                                              bb.keys_a + e0, sort_hist_area(bb.scratch), bb.derr);
       });
     };
     if (device_accessible(src) && device_accessible(dst)) {
@@ -323,22 +426,59 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
       bb.src_dev = bb.dst_dev = nullptr;
     }
 
+    // 2. forward sort
     uint64_t* sorted = nullptr;
-    st = radix_sort_u64(bb.keys_a, bb.keys_b, nkeys, 2 * (int)b, bb.scratch, bb.derr, s, &sorted, true);
+    st = radix_sort_u64(bb.keys_a, bb.keys_b, n_edges, 2 * (int)b, bb.scratch, bb.derr, s, &sorted, true);
     if (st != WEDGE_OK) return bail(st);
+    uint64_t* tkeys = sorted == bb.keys_a ? bb.keys_b : bb.keys_a;
 
-    const int64_t tiles = (nkeys + DEDUP_TILE - 1) / DEDUP_TILE;
-    BUILD_TRY(cudaMemsetAsync(bb.scratch, 0, 256 + (size_t)tiles * sizeof(uint64_t), s), "wedge_graph_build");
-    uint32_t* ctr = static_cast<uint32_t*>(bb.scratch);
-    uint64_t* status = reinterpret_cast<uint64_t*>(static_cast<char*>(bb.scratch) + 256);
+    // 3. unique forward entries, forward counts, transposed keys + their histograms
+    const int tpasses = ((int)b + 7) / 8;
+    const int64_t tiles = (n_edges + DEDUP_TILE - 1) / DEDUP_TILE;
+    if ((st = sort_clear_hist(bb.scratch, s)) != WEDGE_OK) return bail(st);
+    char* tail = static_cast<char*>(bb.scratch) + SORT_MAX_PASSES * 256 * sizeof(uint64_t);  // past the histograms
+    BUILD_TRY(cudaMemsetAsync(tail, 0, 256 + (size_t)tiles * sizeof(uint64_t), s), "wedge_graph_build");
+    uint32_t* ctr = reinterpret_cast<uint32_t*>(tail);
+    uint64_t* status = reinterpret_cast<uint64_t*>(tail + 256);
     st = launch("dedup_rows", s, [&] {
-      k_dedup<<<(unsigned)tiles, DEDUP_THREADS, 0, s>>>(sorted, nkeys, b, n_vertices, sentinel, g->adj, g->deg, status, ctr,
+      k_dedup<<<(unsigned)tiles, DEDUP_THREADS, 0, s>>>(sorted, n_edges, b, n_vertices, sentinel, bb.fwd, tkeys,
+                                                        tpasses, sort_hist_area(bb.scratch), bb.fdeg, status, ctr,
                                                         bb.derr, bb.scalars);
     });
     if (st != WEDGE_OK) return bail(st);
-    st = scan_i32_to_i64(g->deg, g->off, n_vertices, g->off + n_vertices,
-                         reinterpret_cast<int32_t*>(bb.scalars + 1), bb.scratch, bb.derr, s);
+    int64_t m_unique = 0;
+    BUILD_TRY(cudaMemcpyAsync(&m_unique, bb.scalars, sizeof(m_unique), cudaMemcpyDeviceToHost, s), "wedge_graph_build");
+    BUILD_TRY(cudaStreamSynchronize(s), "wedge_graph_build");
+
+    // 4. transposed sort on the larger endpoint's bits; backward counts
+    uint64_t* tsorted = tkeys;
+    st = radix_sort_u64(tkeys, sorted, m_unique, (int)b, bb.scratch, bb.derr, s, &tsorted, true, 32);
     if (st != WEDGE_OK) return bail(st);
+    if (m_unique > 0) {
+      st = launch("count_back", s, [&] {
+        k_count_back<<<grid_stride_blocks(m_unique, 256), 256, 0, s>>>(tsorted, m_unique, bdeg);
+      });
+      if (st != WEDGE_OK) return bail(st);
+    }
+
+    // 5. offsets, degrees and placement
+    st = scan_i32_to_i64(bb.fdeg, bb.foff, n_vertices, bb.foff + n_vertices, nullptr, bb.scratch, bb.derr, s);
+    if (st != WEDGE_OK) return bail(st);
+    st = scan_i32_to_i64(bdeg, boff, n_vertices, boff + n_vertices, nullptr, bb.scratch, bb.derr, s);
+    if (st != WEDGE_OK) return bail(st);
+    int32_t* maxdeg = reinterpret_cast<int32_t*>(bb.scalars + 1);
+    st = launch("row_offsets", s, [&] {
+      k_rows<<<grid_stride_blocks((int64_t)n_vertices + 1, 256), 256, 0, s>>>(bb.fdeg, bdeg, bb.foff, boff, n_vertices,
+                                                                          g->deg, g->off, maxdeg);
+    });
+    if (st != WEDGE_OK) return bail(st);
+    if (m_unique > 0) {
+      st = launch("place_rows", s, [&] {
+        k_place_fwd<<<grid_stride_blocks(m_unique, 256), 256, 0, s>>>(bb.fwd, m_unique, b, boff, g->adj);
+        k_place_back<<<grid_stride_blocks(m_unique, 256), 256, 0, s>>>(tsorted, m_unique, bb.foff, g->adj);
+      });
+      if (st != WEDGE_OK) return bail(st);
+    }
   } else {
     BUILD_TRY(cudaMemsetAsync(g->off, 0, ((size_t)n_vertices + 1) * sizeof(int64_t), s), "wedge_graph_build");
   }
@@ -351,7 +491,7 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
   if (e != cudaSuccess) return bail(cuda_fail(e, "wedge_graph_build"));
   if (herr & DERR_BAD_ID) return bail(fail(WEDGE_EINVAL, "wedge_graph_build: a vertex id is outside [0, %d)", n_vertices));
   if (herr & DERR_TIMEOUT) return bail(fail(WEDGE_ETIMEOUT, "wedge_graph_build: a look-back wait gave up"));
-  g->n_adj = hs[0];
+  g->n_adj = 2 * hs[0];
   g->max_degree = (int32_t)(hs[1] & 0xffffffff);
   if (g->max_degree < 0) g->max_degree = 0;
   *out = g;

@@ -39,8 +39,9 @@ constexpr int SORT_MAX_PASSES = 8;
 size_t sort_scratch_bytes(int64_t n, int bits);
 unsigned long long* sort_hist_area(void* scratch);
 wedge_status sort_clear_hist(void* scratch, cudaStream_t s);
+// Stable LSD sort of the key bits [shift0, shift0 + bits); shift0 a multiple of 8.
 wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, void* scratch, uint32_t* derr,
-                            cudaStream_t s, uint64_t** sorted, bool hist_ready);
+                            cudaStream_t s, uint64_t** sorted, bool hist_ready, int shift0 = 0);
 
 // Exclusive scans with decoupled look-back (scan.cu).
 size_t scan_scratch_bytes(int64_t n);

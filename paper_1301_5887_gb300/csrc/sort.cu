@@ -9,8 +9,9 @@
 // ballots) straight into shared memory in digit order, and writes runs of
 // equal digits contiguously.
 //
-// Only the low `bits` bits are sorted (2 x id bits for packed (u, v) keys),
-// 8 bits per pass; stable, so the result is sorted by the full bit range.
+// Only `bits` bits from bit `shift0` up are sorted (shift0 a multiple of 8),
+// 8 bits per pass; stable, so the result is sorted by that bit range and keeps
+// the input order among equal values.
 #include "device.cuh"
 #include "internal.h"
 #include "runtime.h"
@@ -28,7 +29,7 @@ constexpr int MAX_PASSES = SORT_MAX_PASSES;
 constexpr int HIST_THREADS = 256;
 
 __global__ __launch_bounds__(HIST_THREADS) void k_sort_hist(const uint64_t* __restrict__ keys, int64_t n, int passes,
-                                                            unsigned long long* __restrict__ hist) {
+                                                            uint32_t shift0, unsigned long long* __restrict__ hist) {
   __shared__ uint32_t sh[MAX_PASSES * RADIX];
   for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) sh[i] = 0;
   __syncthreads();
@@ -38,13 +39,14 @@ __global__ __launch_bounds__(HIST_THREADS) void k_sort_hist(const uint64_t* __re
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
     const ulonglong2 kk = __ldcs(k2 + i);
     for (int p = 0; p < passes; ++p) {
-      atomicAdd(&sh[p * RADIX + (uint32_t)((kk.x >> (RADIX_BITS * p)) & (RADIX - 1))], 1u);
-      atomicAdd(&sh[p * RADIX + (uint32_t)((kk.y >> (RADIX_BITS * p)) & (RADIX - 1))], 1u);
+      atomicAdd(&sh[p * RADIX + (uint32_t)((kk.x >> (shift0 + RADIX_BITS * p)) & (RADIX - 1))], 1u);
+      atomicAdd(&sh[p * RADIX + (uint32_t)((kk.y >> (shift0 + RADIX_BITS * p)) & (RADIX - 1))], 1u);
     }
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     const uint64_t k = keys[n - 1];
-    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * RADIX + (uint32_t)((k >> (RADIX_BITS * p)) & (RADIX - 1))], 1u);
+    for (int p = 0; p < passes; ++p)
+      atomicAdd(&sh[p * RADIX + (uint32_t)((k >> (shift0 + RADIX_BITS * p)) & (RADIX - 1))], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
@@ -263,11 +265,12 @@ wedge_status sort_clear_hist(void* scratch, cudaStream_t s) {
 }
 
 wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, void* scratch, uint32_t* derr,
-                            cudaStream_t s, uint64_t** sorted, bool hist_ready) {
+                            cudaStream_t s, uint64_t** sorted, bool hist_ready, int shift0) {
   *sorted = keys;
   if (n <= 1) return WEDGE_OK;
   const int passes = passes_for(bits);
-  if (passes < 1 || passes > MAX_PASSES) return fail(WEDGE_EINVAL, "radix sort: unsupported key width %d", bits);
+  if (passes < 1 || passes > MAX_PASSES || shift0 < 0 || (shift0 & 7) || shift0 + 8 * passes > 64)
+    return fail(WEDGE_EINVAL, "radix sort: unsupported key bits %d from %d", bits, shift0);
   const int64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
   if (tiles > (int64_t)UINT32_MAX) return fail(WEDGE_EINVAL, "radix sort: too many keys (%lld)", (long long)n);
   char* base_ptr = static_cast<char*>(scratch);
@@ -281,7 +284,9 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
   if (!hist_ready) {
     WEDGE_CUDA_TRY(cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, bits), s), "radix sort: clear scratch");
     const int hist_blocks = sm_count() * 8;
-    st = launch("sort_histogram", s, [&] { k_sort_hist<<<hist_blocks, HIST_THREADS, 0, s>>>(keys, n, passes, hist); });
+    st = launch("sort_histogram", s, [&] {
+      k_sort_hist<<<hist_blocks, HIST_THREADS, 0, s>>>(keys, n, passes, (uint32_t)shift0, hist);
+    });
     if (st != WEDGE_OK) return st;
   } else {
     WEDGE_CUDA_TRY(cudaMemsetAsync(base_ptr + hist_bytes, 0, sort_scratch_bytes(n, bits) - hist_bytes, s),
@@ -307,7 +312,7 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
     a.in = src;
     a.out = dst;
     a.n = n;
-    a.shift = (uint32_t)(p * RADIX_BITS);
+    a.shift = (uint32_t)(shift0 + p * RADIX_BITS);
     a.epoch = (uint32_t)(p + 1);
     a.base = digit_base + p * RADIX;
     a.status = status;

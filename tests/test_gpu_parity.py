@@ -381,7 +381,8 @@ def test_profile_counts_launches():
                  "bin_scatter", "sample_closure"]:
         assert st[name]["launches"] >= 1, name
         assert st[name]["total_ms"] > 0.0, name
-    assert st["sort_onesweep_pass"]["launches"] == math.ceil(2 * 10 / 8)
+    # forward keys over 2 x 10 id bits, transposed keys over the larger endpoint's 10 bits
+    assert st["sort_onesweep_pass"]["launches"] == math.ceil(2 * 10 / 8) + math.ceil(10 / 8)
     assert "sort_histogram" not in st  # digit histograms are accumulated by expand_edges
 
 
