@@ -211,15 +211,27 @@ def ncu_figures(kernel):
 
 
 ALG_BYTES = {
-    # algorithmic DRAM bytes per launch, from the sizes of one step
+    # algorithmic DRAM bytes per launch, from the sizes of one step. "nkeys" is
+    # the mean keys per sort pass: 2b-bit forward keys (one per edge) and b-bit
+    # transposed keys (one per unique edge, m = n_adj / 2)
     "sort_onesweep_pass": lambda z: 16 * z["nkeys"],
     "sort_histogram": lambda z: 8 * z["nkeys"],
-    "expand_edges": lambda z: 24 * z["n_edges"],
-    "dedup_rows": lambda z: 8 * z["nkeys"] + 4 * z["n_adj"] + 4 * z["n"],
+    "expand_edges": lambda z: 16 * z["n_edges"],
+    "dedup_rows": lambda z: 8 * z["n_edges"] + 8 * z["n_adj"],
+    "count_back": lambda z: 4 * z["n_adj"],
+    "place_rows": lambda z: 12 * z["n_adj"],
+    "row_offsets": lambda z: 36 * z["n"],
     "scan_degrees": lambda z: 12 * z["n"],
     "bin_count": lambda z: 4 * z["n"],
     "bin_scatter": lambda z: 4 * z["n"] + 12 * z["n2"],
 }
+
+
+def sort_sizes(n_edges, n_adj, id_bits):
+    """Mean keys per sort pass: ceil(2b/8) passes over the forward keys, then
+    ceil(b/8) over the transposed ones."""
+    pf, pt = (2 * id_bits + 7) // 8, (id_bits + 7) // 8
+    return (pf * n_edges + pt * (n_adj // 2)) / (pf + pt)
 
 
 def build_batched_mix(wedge, graphgen, torch, n_graphs=512, seed=3):
@@ -599,7 +611,8 @@ def run_ours(args):
     gwps = world * info["samples"] / (samp_ms / 1e3) / 1e9 if samp_ms > 0 else None
     launches = sum(v["launches"] for v in prof.values())
 
-    sizes = {"nkeys": 2 * n_edges, "n_edges": n_edges, "n_adj": info["n_adj"], "n": n, "n2": info["n2"]}
+    sizes = {"nkeys": sort_sizes(n_edges, info["n_adj"], scale), "n_edges": n_edges, "n_adj": info["n_adj"], "n": n,
+             "n2": info["n2"]}
     top = max((k for k in prof if k in ALG_BYTES), key=lambda k: prof[k]["total_ms"])
     peaks, peak_kind = measured_peaks()
     avg_ms = prof[top]["total_ms"] / prof[top]["launches"]
