@@ -17,11 +17,13 @@
 //      histograms are accumulated on the way.
 //   4. transposed sort: stable LSD radix over bits 32 .. 32 + b only (the
 //      input is already ordered by u), giving the backward entries u of each
-//      row w in ascending order; runs give the backward counts.
-//   5. rows: every backward entry of row x is below x and every forward one
-//      above, so row x is its backward entries followed by its forward ones;
-//      offsets are the sums of the two counts' exclusive scans, and each
-//      entry is written to its final position in one coalesced pass.
+//      row w in ascending order. Every backward entry of row x is below x and
+//      every forward one above, so row x is its backward entries followed by
+//      its forward ones, and the backward entry at sorted position j belongs
+//      at j + (forward entries of earlier rows): the sort's last pass writes
+//      it there and counts the runs of equal w (the backward counts).
+//   5. rows: offsets are the sums of the two counts' exclusive scans; the
+//      forward entries are placed in one coalesced pass.
 #include <algorithm>
 #include <atomic>
 
@@ -394,9 +396,12 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
       return bail(st);
     int32_t* bdeg = bb.fdeg + n_vertices;
     int64_t* boff = bb.foff + (n_vertices + 1);
+    // (the forward-count scan runs past the histogram area, which then holds
+    // the transposed sort's histograms)
+    const size_t hist_bytes = SORT_MAX_PASSES * 256 * sizeof(uint64_t);
     const size_t scratch_bytes =
         std::max(sort_scratch_bytes(n_edges, 2 * (int)b),
-                 std::max(scan_scratch_bytes(n_edges), scan_scratch_bytes(n_vertices)));
+                 std::max(scan_scratch_bytes(n_edges), scan_scratch_bytes(n_vertices) + hist_bytes));
     if ((st = dalloc(&bb.scratch, scratch_bytes, s, "wedge_graph_build: scratch")) != WEDGE_OK) return bail(st);
     BUILD_TRY(cudaMemsetAsync(bb.fdeg, 0, 2 * (size_t)n_vertices * sizeof(int32_t), s), "wedge_graph_build");
 
@@ -436,7 +441,7 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     const int tpasses = ((int)b + 7) / 8;
     const int64_t tiles = (n_edges + DEDUP_TILE - 1) / DEDUP_TILE;
     if ((st = sort_clear_hist(bb.scratch, s)) != WEDGE_OK) return bail(st);
-    char* tail = static_cast<char*>(bb.scratch) + SORT_MAX_PASSES * 256 * sizeof(uint64_t);  // past the histograms
+    char* tail = static_cast<char*>(bb.scratch) + hist_bytes;  // past the histograms
     BUILD_TRY(cudaMemsetAsync(tail, 0, 256 + (size_t)tiles * sizeof(uint64_t), s), "wedge_graph_build");
     uint32_t* ctr = reinterpret_cast<uint32_t*>(tail);
     uint64_t* status = reinterpret_cast<uint64_t*>(tail + 256);
@@ -450,20 +455,26 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     BUILD_TRY(cudaMemcpyAsync(&m_unique, bb.scalars, sizeof(m_unique), cudaMemcpyDeviceToHost, s), "wedge_graph_build");
     BUILD_TRY(cudaStreamSynchronize(s), "wedge_graph_build");
 
-    // 4. transposed sort on the larger endpoint's bits; backward counts
-    uint64_t* tsorted = tkeys;
-    st = radix_sort_u64(tkeys, sorted, m_unique, (int)b, bb.scratch, bb.derr, s, &tsorted, true, 32);
+    // 4. forward offsets; transposed sort on the larger endpoint's bits, its
+    //    last pass placing each backward entry u of row w at j + foff[w] (j
+    //    its sorted position) and counting the backward entries per row
+    st = scan_i32_to_i64(bb.fdeg, bb.foff, n_vertices, bb.foff + n_vertices, nullptr,
+                         static_cast<char*>(bb.scratch) + hist_bytes, bb.derr, s);
     if (st != WEDGE_OK) return bail(st);
-    if (m_unique > 0) {
-      st = launch("count_back", s, [&] {
-        k_count_back<<<grid_stride_blocks(m_unique, 256), 256, 0, s>>>(tsorted, m_unique, bdeg);
+    if (m_unique >= 2) {
+      const SortEmit emit{g->adj, bb.foff, bdeg};
+      uint64_t* unused = nullptr;
+      st = radix_sort_u64(tkeys, sorted, m_unique, (int)b, bb.scratch, bb.derr, s, &unused, true, 32, &emit);
+      if (st != WEDGE_OK) return bail(st);
+    } else if (m_unique == 1) {  // one key is sorted already
+      st = launch("place_rows", s, [&] {
+        k_count_back<<<1, 256, 0, s>>>(tkeys, m_unique, bdeg);
+        k_place_back<<<1, 256, 0, s>>>(tkeys, m_unique, bb.foff, g->adj);
       });
       if (st != WEDGE_OK) return bail(st);
     }
 
-    // 5. offsets, degrees and placement
-    st = scan_i32_to_i64(bb.fdeg, bb.foff, n_vertices, bb.foff + n_vertices, nullptr, bb.scratch, bb.derr, s);
-    if (st != WEDGE_OK) return bail(st);
+    // 5. backward offsets, degrees, forward placement
     st = scan_i32_to_i64(bdeg, boff, n_vertices, boff + n_vertices, nullptr, bb.scratch, bb.derr, s);
     if (st != WEDGE_OK) return bail(st);
     int32_t* maxdeg = reinterpret_cast<int32_t*>(bb.scalars + 1);
@@ -475,7 +486,6 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     if (m_unique > 0) {
       st = launch("place_rows", s, [&] {
         k_place_fwd<<<grid_stride_blocks(m_unique, 256), 256, 0, s>>>(bb.fwd, m_unique, b, boff, g->adj);
-        k_place_back<<<grid_stride_blocks(m_unique, 256), 256, 0, s>>>(tsorted, m_unique, bb.foff, g->adj);
       });
       if (st != WEDGE_OK) return bail(st);
     }

@@ -39,9 +39,21 @@ constexpr int SORT_MAX_PASSES = 8;
 size_t sort_scratch_bytes(int64_t n, int bits);
 unsigned long long* sort_hist_area(void* scratch);
 wedge_status sort_clear_hist(void* scratch, cudaStream_t s);
-// Stable LSD sort of the key bits [shift0, shift0 + bits); shift0 a multiple of 8.
+// Placement by the last pass of a sort of transposed keys (w << 32) | u: the
+// key at sorted position j writes u to adj[j + row_start[w]] and counts one
+// for w in count[w] (instead of being written out).
+struct SortEmit {
+  int32_t* adj;
+  const int64_t* row_start;
+  int32_t* count;
+};
+
+// Stable LSD sort of the key bits [shift0, shift0 + bits); shift0 a multiple
+// of 8. With emit (shift0 >= 32) the last pass places instead of writing keys
+// and *sorted is not meaningful; n must be at least 2.
 wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, void* scratch, uint32_t* derr,
-                            cudaStream_t s, uint64_t** sorted, bool hist_ready, int shift0 = 0);
+                            cudaStream_t s, uint64_t** sorted, bool hist_ready, int shift0 = 0,
+                            const SortEmit* emit = nullptr);
 
 // Exclusive scans with decoupled look-back (scan.cu).
 size_t scan_scratch_bytes(int64_t n);

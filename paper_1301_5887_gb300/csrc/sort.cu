@@ -81,6 +81,7 @@ struct PassArgs {
   uint64_t* status;      // tiles * RADIX look-back words
   uint32_t* tile_ctr;
   uint32_t* err;
+  SortEmit emit;         // last pass of a transposed-key sort: place instead of writing keys
 };
 
 struct PassSmem {
@@ -151,8 +152,11 @@ __device__ __forceinline__ void rank_and_place(PassSmem& sm, const uint64_t (&k)
 //     advances it) and place them in shared memory in digit order;
 //  4. look back for the tile's global digit offsets;
 //  5. write runs of equal digits to their global positions.
-// HI: the pass's digit lies in the keys' high 32-bit half.
-template <bool HI>
+// HI: the pass's digit lies in the keys' high 32-bit half. EMIT (last pass
+// of a sort of transposed keys (w << 32) | u): instead of writing the key to
+// its sorted position j, write u to adj[j + emit.row_start[w]] and add the
+// runs of equal w to emit.count[w].
+template <bool HI, bool EMIT>
 __global__ __launch_bounds__(SORT_THREADS) void k_sort_pass(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PassSmem& sm = *reinterpret_cast<PassSmem*>(smem_raw);
@@ -236,12 +240,38 @@ __global__ __launch_bounds__(SORT_THREADS) void k_sort_pass(PassArgs a) {
   __syncthreads();
 
   // 5. write out in runs
+  if (!EMIT) {
 #pragma unroll
-  for (int i = 0; i < SORT_ITEMS; ++i) {
-    const int pos = i * SORT_THREADS + tid;
-    if (pos < nvalid) {
-      const uint64_t key = sm.keys[pos];
-      __stcs(a.out + (sm.goff[digit_of<HI>(key, sel)] + (uint64_t)pos), key);
+    for (int i = 0; i < SORT_ITEMS; ++i) {
+      const int pos = i * SORT_THREADS + tid;
+      if (pos < nvalid) {
+        const uint64_t key = sm.keys[pos];
+        __stcs(a.out + (sm.goff[digit_of<HI>(key, sel)] + (uint64_t)pos), key);
+      }
+    }
+  } else {
+    // The tile's keys sit in shared memory in their final relative order, and
+    // each digit's keys land on consecutive positions, so equal w form runs
+    // across consecutive lanes.
+    const uint32_t le = lanemask_lt() | (1u << lane);
+#pragma unroll
+    for (int i = 0; i < SORT_ITEMS; ++i) {
+      const int pos = i * SORT_THREADS + tid;
+      uint64_t key = 0;
+      uint32_t w = 0xffffffffu;
+      if (pos < nvalid) {
+        key = sm.keys[pos];
+        w = (uint32_t)(key >> 32);
+        const uint64_t j = sm.goff[digit_of<HI>(key, sel)] + (uint64_t)pos;
+        a.emit.adj[j + __ldg(a.emit.row_start + w)] = (int32_t)(uint32_t)key;
+      }
+      const uint32_t w_prev = __shfl_up_sync(FULL_MASK, w, 1);
+      const uint32_t w_next = __shfl_down_sync(FULL_MASK, w, 1);
+      const uint32_t starts = __ballot_sync(FULL_MASK, lane == 0 || w_prev != w);
+      if (pos < nvalid && (lane == 31 || w_next != w)) {
+        const int start = 31 - __clz(starts & le);
+        atomicAdd(a.emit.count + w, lane - start + 1);
+      }
     }
   }
 }
@@ -265,7 +295,7 @@ wedge_status sort_clear_hist(void* scratch, cudaStream_t s) {
 }
 
 wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, void* scratch, uint32_t* derr,
-                            cudaStream_t s, uint64_t** sorted, bool hist_ready, int shift0) {
+                            cudaStream_t s, uint64_t** sorted, bool hist_ready, int shift0, const SortEmit* emit) {
   *sorted = keys;
   if (n <= 1) return WEDGE_OK;
   const int passes = passes_for(bits);
@@ -297,14 +327,18 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
 
   static bool attr_set = false;
   if (!attr_set) {
-    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)PASS_SMEM),
                    "radix sort: shared memory");
-    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)PASS_SMEM),
+                   "radix sort: shared memory");
+    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)PASS_SMEM),
                    "radix sort: shared memory");
     attr_set = true;
   }
+  if (emit && shift0 < 32) return fail(WEDGE_EINVAL, "radix sort: placement needs keys sorted from bit 32");
   uint64_t* src = keys;
   uint64_t* dst = alt;
   for (int p = 0; p < passes; ++p) {
@@ -318,9 +352,12 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
     a.status = status;
     a.tile_ctr = ctr + p;
     a.err = derr;
+    a.emit = emit ? *emit : SortEmit{};
+    const bool place = emit && p == passes - 1;
     st = launch("sort_onesweep_pass", s, [&] {
-      if (a.shift >= 32) k_sort_pass<true><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
-      else k_sort_pass<false><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
+      if (place) k_sort_pass<true, true><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
+      else if (a.shift >= 32) k_sort_pass<true, false><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
+      else k_sort_pass<false, false><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
     });
     if (st != WEDGE_OK) return st;
     uint64_t* t = src;
