@@ -218,8 +218,7 @@ ALG_BYTES = {
     "sort_histogram": lambda z: 8 * z["nkeys"],
     "expand_edges": lambda z: 16 * z["n_edges"],
     "dedup_rows": lambda z: 8 * z["n_edges"] + 8 * z["n_adj"],
-    "count_back": lambda z: 4 * z["n_adj"],
-    "place_rows": lambda z: 12 * z["n_adj"],
+    "place_rows": lambda z: 6 * z["n_adj"],
     "row_offsets": lambda z: 36 * z["n"],
     "scan_degrees": lambda z: 12 * z["n"],
     "bin_count": lambda z: 4 * z["n"],
