@@ -53,12 +53,13 @@ __device__ __forceinline__ int32_t row_of(const int64_t* __restrict__ off, int32
   return lo;
 }
 
-// Row of entry e, given a row u with off[u] <= e: a few steps forward (the
-// common case), then a binary search, so long runs of empty rows cost
-// O(log n) instead of one step each.
+// Row of entry e, given a row u with off[u] <= e: up to 32 steps forward
+// over consecutive (cached) offsets, the common case even with isolated
+// vertices, then a binary search, so a long run of empty rows costs O(log n)
+// instead of one step each.
 __device__ __forceinline__ int32_t next_row(const int64_t* __restrict__ off, int32_t n, int32_t u, int64_t e) {
 #pragma unroll 1
-  for (int t = 0; t < 4; ++t) {
+  for (int t = 0; t < 32; ++t) {
     if (e < __ldg(off + u + 1)) return u;
     ++u;
   }
@@ -374,12 +375,13 @@ __global__ __launch_bounds__(TC_THREADS) void k_tri_hash_warp(CountArgs a) {
 // memory when d+(u) <= SLOTS / 2; a longer row searches N+(u) in global
 // memory instead (degree order bounds d+ by about sqrt(2m), so this is rare).
 // The rows N+(v), v in N+(u), are streamed in chunks of SLOTS / 2
-// out-neighbours as one flattened work list; each thread keeps ILP items in
-// flight.
+// out-neighbours as one flattened work list. (The walker code allows several
+// items in flight per thread; one measured fastest: fewer registers, more
+// resident warps.)
 template <int THREADS, int SLOTS>
 __global__ __launch_bounds__(THREADS) void k_tri_hash_cta(CountArgs a, const int32_t* __restrict__ list,
                                                           int32_t n_list, unsigned int* ticket) {
-  constexpr int ILP = 4;
+  constexpr int ILP = 1;
   constexpr int CHUNK = SLOTS / 2;
   extern __shared__ __align__(16) unsigned char dyn[];
   int32_t* table = reinterpret_cast<int32_t*>(dyn);
@@ -524,7 +526,7 @@ __global__ __launch_bounds__(THREADS) void k_tri_hash_cta(CountArgs a, const int
 }
 
 constexpr int MID_THREADS = 256, MID_SLOTS = 2048;    // 128 < d+ <= 1024
-constexpr int BIG_THREADS = 256, BIG_SLOTS = 8192;    // d+ > 1024 (table for d+ <= 4096)
+constexpr int BIG_THREADS = 512, BIG_SLOTS = 8192;    // d+ > 1024 (table for d+ <= 4096)
 
 template <int THREADS, int SLOTS>
 constexpr size_t cta_smem() {
