@@ -744,7 +744,10 @@ def run_ours(args):
                            "bins": info["n_bins"], "samples_per_step": info["samples"],
                            "l2": f"inputs {8 * n_edges / 1e9:.1f} GB > 129 MB L2, no flush needed",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "gwedges_checked_per_s": gwps, "sampling_ms": samp_ms, "batched": batched, "serving": serving,
+                "gwedges_checked_per_s": gwps, "sampling_ms": samp_ms,
+                "s_per_M_generated_edges": {"device": (ms_step / 1e3) / (world * n_edges / 1e6),
+                                            "e2e": (e2e["ms_per_step"] / 1e3) / (world * n_edges / 1e6)
+                                            if e2e else None}, "batched": batched, "serving": serving,
                 "triangle_stats": tri, "rounding": rounding, "sorted_closure": sorted_cl, "roofline": roofline, "sampling_roofline": sampling_roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
                 "clocks": clk, "kernels": kernels,
                 "estimates": {"c_hat": info["c_hat"], "c_hat_global": info["c_hat_global"]}}
