@@ -656,6 +656,17 @@ def run_ours(args):
         hsrc.copy_(src)
         hdst.copy_(dst)
         torch.cuda.synchronize()
+        # The host link's rate right now (its share of the node's host memory
+        # bandwidth varies with the other tenants): a plain copy of the same
+        # pinned inputs back over the device arrays, which hold the same values.
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        src.copy_(hsrc, non_blocking=True)
+        dst.copy_(hdst, non_blocking=True)
+        l1.record(stream)
+        torch.cuda.synchronize()
+        link_gbs = 8 * n_edges / (l0.elapsed_time(l1) / 1e3) / 1e9
         step(hsrc, hdst)  # warm the staging path
         torch.cuda.synchronize()
         times = []
@@ -673,7 +684,8 @@ def run_ours(args):
             dt = float(t.item())
         d2h = 8 + 16 + 2 * 8 * info["n_bins"] + 4 + 8 * (4 * info["n_streams"] + 34 * 34)
         e2e = {"value": dt / (world * m / 1e6), "unit": "s/Medge", "h2d_bytes_per_step": 8 * n_edges,
-               "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "step_ms": [x * 1e3 for x in times]}
+               "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "step_ms": [x * 1e3 for x in times],
+               "h2d_link_gbs": link_gbs}
         del hsrc, hdst
 
     # Triangle statistics (Sec. 5.7): k global-stream samples, closed ones

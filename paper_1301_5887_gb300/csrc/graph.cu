@@ -38,9 +38,28 @@ constexpr int DEDUP_THREADS = 256;
 constexpr int DEDUP_ITEMS = 16;
 constexpr int DEDUP_TILE = DEDUP_THREADS * DEDUP_ITEMS;
 
-// Expand edges to packed keys (min << b) | max and accumulate the radix
-// sort's digit histograms (8-bit digits, `passes` of them) in shared memory
-// on the way.
+// Packed forward key of input pair (u, v): (min << b) | max, or the sentinel
+// for a self-loop or an id outside [0, n) (the latter raising DERR_BAD_ID).
+__device__ __forceinline__ uint64_t edge_key(int32_t u, int32_t v, int32_t n, uint32_t b, uint64_t sentinel,
+                                             uint32_t* err) {
+  if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
+    atomicOr(err, DERR_BAD_ID);
+    return sentinel;
+  }
+  if (u == v) return sentinel;
+  return u < v ? ((uint64_t)u << b) | (uint64_t)v : ((uint64_t)v << b) | (uint64_t)u;
+}
+
+__device__ __forceinline__ void count_digits(uint32_t* sh, uint64_t key, int passes) {
+  for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + (uint32_t)((key >> (8 * p)) & 255u)], 1u);
+}
+
+// Expand edges to packed keys and accumulate the radix sort's digit
+// histograms (8-bit digits, `passes` of them) in shared memory on the way.
+// VEC: src, dst and keys are 16-byte aligned, and each thread takes four
+// edges per step with 16-byte loads (the scalar form keeps too few bytes in
+// flight to stream at the HBM rate).
+template <bool VEC>
 __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                                                 int64_t m, int32_t n, uint32_t b, uint64_t sentinel, int passes,
                                                 uint64_t* __restrict__ keys, unsigned long long* __restrict__ hist,
@@ -49,19 +68,30 @@ __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src,
   for (int i = threadIdx.x; i < SORT_MAX_PASSES * 256; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-    const int32_t u = __ldcs(src + e), v = __ldcs(dst + e);
-    uint64_t key;
-    if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
-      atomicOr(err, DERR_BAD_ID);
-      key = sentinel;
-    } else if (u == v) {
-      key = sentinel;
-    } else {
-      key = u < v ? ((uint64_t)u << b) | (uint64_t)v : ((uint64_t)v << b) | (uint64_t)u;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t scalar_from = 0;
+  if (VEC) {
+    const int64_t m4 = m >> 2;
+    const int4* s4 = reinterpret_cast<const int4*>(src);
+    const int4* d4 = reinterpret_cast<const int4*>(dst);
+    ulonglong2* k2 = reinterpret_cast<ulonglong2*>(keys);
+    for (int64_t e = t0; e < m4; e += stride) {
+      const int4 u = __ldcs(s4 + e), v = __ldcs(d4 + e);
+      const uint64_t k0 = edge_key(u.x, v.x, n, b, sentinel, err), k1 = edge_key(u.y, v.y, n, b, sentinel, err);
+      const uint64_t k2v = edge_key(u.z, v.z, n, b, sentinel, err), k3 = edge_key(u.w, v.w, n, b, sentinel, err);
+      __stcs(k2 + 2 * e, make_ulonglong2(k0, k1));
+      __stcs(k2 + 2 * e + 1, make_ulonglong2(k2v, k3));
+      count_digits(sh, k0, passes);
+      count_digits(sh, k1, passes);
+      count_digits(sh, k2v, passes);
+      count_digits(sh, k3, passes);
     }
+    scalar_from = m4 << 2;  // the last m mod 4 edges
+  }
+  for (int64_t e = scalar_from + t0; e < m; e += stride) {
+    const uint64_t key = edge_key(__ldcs(src + e), __ldcs(dst + e), n, b, sentinel, err);
     __stcs(keys + e, key);
-    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + (uint32_t)((key >> (8 * p)) & 255u)], 1u);
+    count_digits(sh, key, passes);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
@@ -211,13 +241,22 @@ __global__ __launch_bounds__(256) void k_rows(const int32_t* __restrict__ fdeg, 
 
 // Forward entry i, key (u << b) | w, goes to i + boff[u + 1]: row u starts at
 // foff[u] + boff[u] and holds its boff[u + 1] - boff[u] backward entries first.
+// A warp places 128 consecutive entries per step, each lane four of them 32
+// apart, so every load and store instruction stays coalesced while four
+// loads per thread are in flight.
 __global__ __launch_bounds__(256) void k_place_fwd(const uint64_t* __restrict__ fwd, int64_t m, uint32_t b,
                                                    const int64_t* __restrict__ boff, int32_t* __restrict__ adj) {
   const uint64_t vmask = (1ULL << b) - 1ULL;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-    const uint64_t key = __ldcs(fwd + i);
-    adj[i + __ldg(boff + (key >> b) + 1)] = (int32_t)(key & vmask);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane) * 4;  // this warp's first entry
+  const int64_t step = (int64_t)gridDim.x * blockDim.x * 4;
+  for (int64_t i0 = warp0 + lane; i0 < m; i0 += step) {
+    uint64_t k[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) k[r] = i0 + 32 * r < m ? __ldcs(fwd + i0 + 32 * r) : 0ULL;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (i0 + 32 * r < m) adj[i0 + 32 * r + __ldg(boff + (k[r] >> b) + 1)] = (int32_t)(k[r] & vmask);
   }
 }
 
@@ -409,9 +448,19 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     const int passes = (2 * (int)b + 7) / 8;
     if ((st = sort_clear_hist(bb.scratch, s)) != WEDGE_OK) return bail(st);
     auto expand = [&](const int32_t* s_in, const int32_t* d_in, int64_t e0, int64_t len) {
+      uint64_t* k_out = bb.keys_a + e0;
+      const bool vec = ((reinterpret_cast<uintptr_t>(s_in) | reinterpret_cast<uintptr_t>(d_in) |
+                         reinterpret_cast<uintptr_t>(k_out)) & 15) == 0;
+      // twice the usual grid: more resident loads in flight
+      const int64_t units = vec ? (len + 3) / 4 : len;
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((units + 255) / 256, (int64_t)sm_count() * 16));
       return launch("expand_edges", s, [&] {
-        k_expand<<<grid_stride_blocks(len, 256), 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes,
-                                                              bb.keys_a + e0, sort_hist_area(bb.scratch), bb.derr);
+        if (vec)
+          k_expand<true><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out,
+                                              sort_hist_area(bb.scratch), bb.derr);
+        else
+          k_expand<false><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out,
+                                               sort_hist_area(bb.scratch), bb.derr);
       });
     };
     if (device_accessible(src) && device_accessible(dst)) {
@@ -485,7 +534,9 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     if (st != WEDGE_OK) return bail(st);
     if (m_unique > 0) {
       st = launch("place_rows", s, [&] {
-        k_place_fwd<<<grid_stride_blocks(m_unique, 256), 256, 0, s>>>(bb.fwd, m_unique, b, boff, g->adj);
+        const int64_t want = (m_unique / 4 + 255) / 256;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * 16));
+        k_place_fwd<<<grid, 256, 0, s>>>(bb.fwd, m_unique, b, boff, g->adj);
       });
       if (st != WEDGE_OK) return bail(st);
     }
