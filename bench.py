@@ -485,6 +485,7 @@ def bench_rounding(wedge, graphgen, torch, g, b, iid_sampling_ms, reps=3, var_sc
     spread = {}
     for key in est:
         a = np.array(est[key])
+        a = a[:, np.isfinite(a).sum(axis=0) >= 2]  # bins sampled under at least two seeds
         m = np.nanmean(a, axis=0)
         sd = np.nanstd(a, axis=0, ddof=1)
         ok = m > 0
