@@ -223,6 +223,7 @@ ALG_BYTES = {
     "scan_degrees": lambda z: 12 * z["n"],
     "bin_count": lambda z: 4 * z["n"],
     "bin_scatter": lambda z: 4 * z["n"] + 12 * z["n2"],
+    "scan_bin_wedges": lambda z: 16 * z["n2"],
 }
 
 

@@ -2,11 +2,13 @@
 //
 // Sec. 4.2 defines the bins; Alg. Phase 1b sums, per bin, the vertex count
 // n_b and the wedge count p_b = sum C(d,2). Here one pass over the degree
-// array counts per (bin, tile) in shared memory, two exclusive scans over the
-// bin-major (bin, tile) matrices give every tile its output position and
-// wedge prefix in each bin, and a second pass writes the vertices of degree
-// >= 2 in (bin, id) order (L) together with the running wedge prefix (W).
-// W is what the sampler's inverse-CDF centre search runs on (Sec. 3.2).
+// array counts per (bin, tile) in shared memory, an exclusive scan over the
+// bin-major (bin, tile) count matrix gives every tile its output position in
+// each bin, and a second pass writes the vertices of degree >= 2 in (bin, id)
+// order (L) beside their wedge counts C(d,2); one exclusive scan of those
+// gives the running wedge prefix W over L (W[j] - W[start of bin b] is the
+// wedge prefix within bin b). W is what the sampler's inverse-CDF centre
+// search runs on (Sec. 3.2).
 #include <string.h>
 
 #include <vector>
@@ -26,17 +28,13 @@ constexpr int BIN_TILE = BIN_THREADS * BIN_ITEMS;
 __global__ __launch_bounds__(BIN_THREADS) void k_bin_count(const int32_t* __restrict__ deg, int32_t n,
                                                            const uint64_t* __restrict__ lo_g, uint32_t nb,
                                                            uint32_t pow2, int64_t n_tiles, uint32_t* __restrict__ mat_cnt,
-                                                           uint64_t* __restrict__ mat_w,
-                                                           unsigned long long* __restrict__ n_b,
-                                                           unsigned long long* __restrict__ p_b) {
+                                                           unsigned long long* __restrict__ n_b) {
   __shared__ uint64_t s_lo[WEDGE_MAX_BINS];
   __shared__ uint32_t s_n[WEDGE_MAX_BINS];
-  __shared__ unsigned long long s_w[WEDGE_MAX_BINS];
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x;
   for (int i = tid; i < (int)nb; i += BIN_THREADS) {
     s_lo[i] = lo_g[i];
     s_n[i] = 0;
-    s_w[i] = 0;
   }
   __syncthreads();
   const BinTable t{s_lo, nb, pow2};
@@ -48,55 +46,46 @@ __global__ __launch_bounds__(BIN_THREADS) void k_bin_count(const int32_t* __rest
     const int32_t d = v < n ? __ldg(deg + v) : 0;
     const uint32_t b = d > 0 ? bin_of(t, (uint64_t)d) : 0xffffffffu;
     const uint32_t peers = __match_any_sync(FULL_MASK, b);
-    if (b != 0xffffffffu) {
-      if ((peers & lanemask_lt()) == 0) atomicAdd(&s_n[b], (uint32_t)__popc(peers));
-      if (d >= 2) atomicAdd(&s_w[b], (unsigned long long)d * (unsigned long long)(d - 1) / 2ULL);
-    }
-    (void)lane;
+    if (b != 0xffffffffu && (peers & lanemask_lt()) == 0) atomicAdd(&s_n[b], (uint32_t)__popc(peers));
   }
   __syncthreads();
   for (int b = tid; b < (int)nb; b += BIN_THREADS) {
     // bins >= 2 hold exactly the vertices of degree >= 2 (bin 1 is {1})
     mat_cnt[(int64_t)b * n_tiles + tile] = b >= 2 ? s_n[b] : 0u;
-    mat_w[(int64_t)b * n_tiles + tile] = b >= 2 ? (uint64_t)s_w[b] : 0ULL;
     if (s_n[b]) atomicAdd(&n_b[b], (unsigned long long)s_n[b]);
-    if (s_w[b]) atomicAdd(&p_b[b], s_w[b]);
   }
 }
 
-// Sum over the lanes in `peers` of x (tot) and over those below this lane (pre).
-__device__ __forceinline__ void group_sums(uint32_t peers, uint64_t x, int lane, uint64_t& tot, uint64_t& pre) {
-  tot = 0;
-  pre = 0;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const uint64_t y = __shfl_sync(FULL_MASK, x, j);
-    if ((peers >> j) & 1u) {
-      tot += y;
-      if (j < lane) pre += y;
-    }
+// W at the bin boundaries: bound[k] = W[start of bin k], k = 0 .. nb (bins 0
+// and 1 hold no vertex of L; bin k >= 2 starts after the n_b of bins 2..k-1),
+// so p_b = bound[b + 1] - bound[b].
+__global__ void k_bin_bounds(const unsigned long long* __restrict__ n_b, uint32_t nb, const uint64_t* __restrict__ W,
+                             unsigned long long* __restrict__ bound) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t start = 0;
+  for (uint32_t k = 0; k <= nb; ++k) {
+    bound[k] = W[start];
+    if (k >= 2 && k < nb) start += (int64_t)n_b[k];
   }
 }
 
+// Second pass: the vertices of degree >= 2 of each (bin, tile) go to the
+// tile's position in the bin, in id order (a warp's lanes hold consecutive
+// ids, and its peers in a bin are ranked by lane), with C(d,2) beside them.
 __global__ __launch_bounds__(BIN_THREADS) void k_bin_scatter(const int32_t* __restrict__ deg, int32_t n,
                                                              const uint64_t* __restrict__ lo_g, uint32_t nb,
                                                              uint32_t pow2, int64_t n_tiles,
                                                              const int64_t* __restrict__ pos_base,
-                                                             const uint64_t* __restrict__ w_base,
-                                                             int32_t* __restrict__ L, uint64_t* __restrict__ W) {
+                                                             int32_t* __restrict__ L, uint64_t* __restrict__ wedges) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* s_lo = reinterpret_cast<uint64_t*>(smem);
-  int64_t* s_pos = reinterpret_cast<int64_t*>(s_lo + nb);      // [warp][bin]
-  uint64_t* s_wp = reinterpret_cast<uint64_t*>(s_pos + BIN_WARPS * nb);
-  int32_t* s_deg = reinterpret_cast<int32_t*>(s_wp + BIN_WARPS * nb);
+  int64_t* s_pos = reinterpret_cast<int64_t*>(s_lo + nb);  // [warp][bin]
+  int32_t* s_deg = reinterpret_cast<int32_t*>(s_pos + BIN_WARPS * nb);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t tile = blockIdx.x;
   const int64_t tbase = tile * BIN_TILE;
   for (int i = tid; i < (int)nb; i += BIN_THREADS) s_lo[i] = lo_g[i];
-  for (int i = tid; i < BIN_WARPS * (int)nb; i += BIN_THREADS) {
-    s_pos[i] = 0;
-    s_wp[i] = 0;
-  }
+  for (int i = tid; i < BIN_WARPS * (int)nb; i += BIN_THREADS) s_pos[i] = 0;
   for (int i = tid; i < BIN_TILE; i += BIN_THREADS) {
     const int64_t v = tbase + i;
     s_deg[i] = v < n ? __ldg(deg + v) : 0;
@@ -104,59 +93,40 @@ __global__ __launch_bounds__(BIN_THREADS) void k_bin_scatter(const int32_t* __re
   __syncthreads();
   const BinTable t{s_lo, nb, pow2};
   const uint32_t lt = lanemask_lt();
-  // Pass A: per-warp counts and wedge sums over the warp's 512 consecutive ids.
+  // Pass A: per-warp counts over the warp's 512 consecutive ids.
   for (int r = 0; r < BIN_ITEMS; ++r) {
-    const int vl = warp * (32 * BIN_ITEMS) + r * 32 + lane;
-    const int32_t d = s_deg[vl];
+    const int32_t d = s_deg[warp * (32 * BIN_ITEMS) + r * 32 + lane];
     const uint32_t b = d >= 2 ? bin_of(t, (uint64_t)d) : 0xffffffffu;
-    const uint64_t w = d >= 2 ? (uint64_t)d * (uint64_t)(d - 1) / 2ULL : 0ULL;
     const uint32_t peers = __match_any_sync(FULL_MASK, b);
-    uint64_t tot, pre;
-    group_sums(peers, w, lane, tot, pre);
-    if (b != 0xffffffffu && (peers & lt) == 0) {
-      s_pos[warp * nb + b] += __popc(peers);
-      s_wp[warp * nb + b] += tot;
-    }
+    if (b != 0xffffffffu && (peers & lt) == 0) s_pos[warp * nb + b] += __popc(peers);
     __syncwarp();
   }
   __syncthreads();
   // Per bin: running start of each warp = tile base + earlier warps.
   for (int b = tid; b < (int)nb; b += BIN_THREADS) {
     int64_t pos = pos_base[(int64_t)b * n_tiles + tile];
-    uint64_t wp = w_base[(int64_t)b * n_tiles + tile];
     for (int w = 0; w < BIN_WARPS; ++w) {
       const int64_t c = s_pos[w * nb + b];
-      const uint64_t x = s_wp[w * nb + b];
       s_pos[w * nb + b] = pos;
-      s_wp[w * nb + b] = wp;
       pos += c;
-      wp += x;
     }
   }
   __syncthreads();
-  // Pass B: write L and W in id order within each bin.
+  // Pass B: write L and the wedge counts in id order within each bin.
   for (int r = 0; r < BIN_ITEMS; ++r) {
     const int vl = warp * (32 * BIN_ITEMS) + r * 32 + lane;
     const int32_t d = s_deg[vl];
     const uint32_t b = d >= 2 ? bin_of(t, (uint64_t)d) : 0xffffffffu;
-    const uint64_t w = d >= 2 ? (uint64_t)d * (uint64_t)(d - 1) / 2ULL : 0ULL;
     const uint32_t peers = __match_any_sync(FULL_MASK, b);
-    uint64_t tot, pre;
-    group_sums(peers, w, lane, tot, pre);
     int64_t p0 = 0;
-    uint64_t w0 = 0;
     if (b != 0xffffffffu) {
       p0 = s_pos[warp * nb + b];
-      w0 = s_wp[warp * nb + b];
       const int64_t pos = p0 + __popc(peers & lt);
       L[pos] = (int32_t)(tbase + vl);
-      W[pos] = w0 + pre;
+      wedges[pos] = (uint64_t)d * (uint64_t)(d - 1) / 2ULL;
     }
     __syncwarp();
-    if (b != 0xffffffffu && (peers & lt) == 0) {
-      s_pos[warp * nb + b] = p0 + __popc(peers);
-      s_wp[warp * nb + b] = w0 + tot;
-    }
+    if (b != 0xffffffffu && (peers & lt) == 0) s_pos[warp * nb + b] = p0 + __popc(peers);
     __syncwarp();
   }
 }
@@ -237,24 +207,21 @@ extern "C" wedge_status wedge_bin(const wedge_graph* g, const wedge_bin_params* 
   b->W = nullptr;
   b->lo_dev = nullptr;
   uint32_t* mat_cnt = nullptr;
-  uint64_t* mat_w = nullptr;
   int64_t* pos_base = nullptr;
-  uint64_t* w_base = nullptr;
-  unsigned long long* sums = nullptr;  // n_b[nb], p_b[nb]
+  uint64_t* wedges = nullptr;  // C(d,2) per entry of L, scanned into W
+  unsigned long long* sums = nullptr;  // n_b[nb], then W at the nb + 1 bin boundaries
   void* scratch = nullptr;
   uint32_t* derr = nullptr;
   auto release_tmp = [&]() {
     dfree(mat_cnt, s);
-    dfree(mat_w, s);
     dfree(pos_base, s);
-    dfree(w_base, s);
+    dfree(wedges, s);
     dfree(sums, s);
     dfree(scratch, s);
     dfree(derr, s);
     mat_cnt = nullptr;
-    mat_w = nullptr;
     pos_base = nullptr;
-    w_base = nullptr;
+    wedges = nullptr;
     sums = nullptr;
     scratch = nullptr;
     derr = nullptr;
@@ -271,27 +238,23 @@ extern "C" wedge_status wedge_bin(const wedge_graph* g, const wedge_bin_params* 
   wedge_status st;
   if ((st = dalloc_n(&b->lo_dev, nb, s, "wedge_bin")) != WEDGE_OK) return bail(st);
   if ((st = dalloc_n(&mat_cnt, (size_t)mat, s, "wedge_bin")) != WEDGE_OK) return bail(st);
-  if ((st = dalloc_n(&mat_w, (size_t)mat, s, "wedge_bin")) != WEDGE_OK) return bail(st);
   if ((st = dalloc_n(&pos_base, (size_t)mat, s, "wedge_bin")) != WEDGE_OK) return bail(st);
-  if ((st = dalloc_n(&w_base, (size_t)mat, s, "wedge_bin")) != WEDGE_OK) return bail(st);
-  if ((st = dalloc_n(&sums, 2 * (size_t)nb, s, "wedge_bin")) != WEDGE_OK) return bail(st);
+  if ((st = dalloc_n(&sums, 2 * (size_t)nb + 1, s, "wedge_bin")) != WEDGE_OK) return bail(st);
   if ((st = dalloc(&scratch, scan_scratch_bytes(mat), s, "wedge_bin")) != WEDGE_OK) return bail(st);
   if ((st = dalloc_n(&derr, 64, s, "wedge_bin")) != WEDGE_OK) return bail(st);
   BIN_TRY(cudaMemcpyAsync(b->lo_dev, lo.data(), nb * sizeof(uint64_t), cudaMemcpyHostToDevice, s), "wedge_bin");
-  BIN_TRY(cudaMemsetAsync(sums, 0, 2 * nb * sizeof(uint64_t), s), "wedge_bin");
+  BIN_TRY(cudaMemsetAsync(sums, 0, (2 * nb + 1) * sizeof(uint64_t), s), "wedge_bin");
   BIN_TRY(cudaMemsetAsync(derr, 0, 64 * sizeof(uint32_t), s), "wedge_bin");
 
   st = launch("bin_count", s, [&] {
-    k_bin_count<<<(unsigned)n_tiles, BIN_THREADS, 0, s>>>(g->deg, n, b->lo_dev, nb, b->pow2, n_tiles, mat_cnt, mat_w,
-                                                          sums, sums + nb);
+    k_bin_count<<<(unsigned)n_tiles, BIN_THREADS, 0, s>>>(g->deg, n, b->lo_dev, nb, b->pow2, n_tiles, mat_cnt, sums);
   });
   if (st != WEDGE_OK) return bail(st);
   if ((st = scan_u32_to_i64(mat_cnt, pos_base, mat, scratch, derr, s)) != WEDGE_OK) return bail(st);
-  if ((st = scan_u64_to_u64(mat_w, w_base, mat, scratch, derr, s)) != WEDGE_OK) return bail(st);
 
-  std::vector<unsigned long long> hs(2 * nb);
+  std::vector<unsigned long long> hs(2 * nb + 1);
   uint32_t herr = 0;
-  BIN_TRY(cudaMemcpyAsync(hs.data(), sums, 2 * nb * sizeof(uint64_t), cudaMemcpyDeviceToHost, s), "wedge_bin");
+  BIN_TRY(cudaMemcpyAsync(hs.data(), sums, nb * sizeof(uint64_t), cudaMemcpyDeviceToHost, s), "wedge_bin");
   BIN_TRY(cudaMemcpyAsync(&herr, derr, sizeof(herr), cudaMemcpyDeviceToHost, s), "wedge_bin");
   BIN_TRY(cudaStreamSynchronize(s), "wedge_bin");
   if (herr & DERR_TIMEOUT) return bail(fail(WEDGE_ETIMEOUT, "wedge_bin: a look-back wait gave up"));
@@ -301,33 +264,49 @@ extern "C" wedge_status wedge_bin(const wedge_graph* g, const wedge_bin_params* 
   inf.tau = bp->tau;
   inf.omega = bp->omega;
   int64_t n2 = 0;
-  uint64_t p = 0;
   for (uint32_t k = 0; k < nb; ++k) {
     inf.lo_deg[k] = lo[k];
     inf.hi_deg[k] = lo[k + 1] == UINT64_MAX ? UINT64_MAX : lo[k + 1] - 1;
     inf.n_b[k] = hs[k];
-    inf.p_b[k] = hs[nb + k];
     inf.start[k] = n2;
     if (k >= 2) n2 += (int64_t)hs[k];
-    p += hs[nb + k];
   }
   for (uint32_t k = nb; k <= WEDGE_MAX_BINS; ++k) inf.start[k] = n2;
-  inf.p_total = p;
   inf.n_wedge_vertices = n2;
 
   if ((st = dalloc_n(&b->L, (size_t)(n2 > 0 ? n2 : 1), s, "wedge_bin: L")) != WEDGE_OK) return bail(st);
   if ((st = dalloc_n(&b->W, (size_t)n2 + 1, s, "wedge_bin: W")) != WEDGE_OK) return bail(st);
   if (n2 > 0) {
-    const size_t smem = nb * sizeof(uint64_t) + 2 * BIN_WARPS * nb * sizeof(uint64_t) + BIN_TILE * sizeof(int32_t);
+    if ((st = dalloc_n(&wedges, (size_t)n2, s, "wedge_bin")) != WEDGE_OK) return bail(st);
+    const size_t smem = nb * sizeof(uint64_t) + BIN_WARPS * nb * sizeof(int64_t) + BIN_TILE * sizeof(int32_t);
     BIN_TRY(cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "wedge_bin");
     st = launch("bin_scatter", s, [&] {
       k_bin_scatter<<<(unsigned)n_tiles, BIN_THREADS, smem, s>>>(g->deg, n, b->lo_dev, nb, b->pow2, n_tiles, pos_base,
-                                                                 w_base, b->L, b->W);
+                                                                 b->L, wedges);
     });
     if (st != WEDGE_OK) return bail(st);
+    // W = exclusive prefix of the wedge counts over L, W[n2] = p
+    if (scan_scratch_bytes(n2) > scan_scratch_bytes(mat)) {
+      dfree(scratch, s);
+      scratch = nullptr;
+      if ((st = dalloc(&scratch, scan_scratch_bytes(n2), s, "wedge_bin")) != WEDGE_OK) return bail(st);
+    }
+    if ((st = scan_u64_with_total(wedges, b->W, n2, scratch, derr, s, "scan_bin_wedges")) != WEDGE_OK)
+      return bail(st);
+    st = launch("bin_bounds", s, [&] { k_bin_bounds<<<1, 32, 0, s>>>(sums, nb, b->W, sums + nb); });
+    if (st != WEDGE_OK) return bail(st);
+    BIN_TRY(cudaMemcpyAsync(hs.data() + nb, sums + nb, (nb + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s),
+            "wedge_bin");
+    BIN_TRY(cudaMemcpyAsync(&herr, derr, sizeof(herr), cudaMemcpyDeviceToHost, s), "wedge_bin");
+  } else {
+    BIN_TRY(cudaMemsetAsync(b->W, 0, sizeof(uint64_t), s), "wedge_bin");
+    for (uint32_t k = 0; k <= nb; ++k) hs[nb + k] = 0;
   }
-  BIN_TRY(cudaMemcpyAsync(b->W + n2, &inf.p_total, sizeof(uint64_t), cudaMemcpyHostToDevice, s), "wedge_bin");
   BIN_TRY(cudaStreamSynchronize(s), "wedge_bin");
+  if (herr & DERR_TIMEOUT) return bail(fail(WEDGE_ETIMEOUT, "wedge_bin: a look-back wait gave up"));
+  // p_b: the wedge prefix across bin b's stretch of L
+  for (uint32_t k = 0; k < nb; ++k) inf.p_b[k] = hs[nb + k + 1] - hs[nb + k];
+  inf.p_total = hs[2 * nb];
   release_tmp();
   inf.L = b->L;
   inf.W = b->W;
