@@ -11,10 +11,11 @@
 //      appear. A host edge list streams through two device staging slots,
 //      its transfer overlapping the expansion of the previous chunk.
 //   2. sort: LSD radix over the 2b significant bits.
-//   3. dedup: adjacent-unique keys (u, w), u < w, become the forward entries
-//      w of row u (compacted in order; one atomic per run of equal u per warp
-//      counts them) and the transposed keys (w << 32) | u, whose digit
-//      histograms are accumulated on the way.
+//   3. dedup: adjacent-unique keys (u, w), u < w, are the forward entries w
+//      of row u (one atomic per run of equal u per warp counts them); they
+//      become the transposed keys (w << 32) | u, compacted in order, whose
+//      digit histograms are accumulated on the way, and each tile records
+//      how many unique keys precede it.
 //   4. transposed sort: stable LSD radix over bits 32 .. 32 + b only (the
 //      input is already ordered by u), giving the backward entries u of each
 //      row w in ascending order. Every backward entry of row x is below x and
@@ -23,7 +24,8 @@
 //      at j + (forward entries of earlier rows): the sort's last pass writes
 //      it there and counts the runs of equal w (the backward counts).
 //   5. rows: offsets are the sums of the two counts' exclusive scans; the
-//      forward entries are placed in one coalesced pass.
+//      forward entries are placed in one coalesced pass over the sorted keys,
+//      which are still intact (the transposed sort ran in other buffers).
 #include <algorithm>
 #include <atomic>
 
@@ -98,15 +100,46 @@ __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src,
     if (sh[i]) atomicAdd(&hist[i], (unsigned long long)sh[i]);
 }
 
-// Adjacent-unique of sorted forward keys (u, w) -> unique forward keys (in
-// order), forward row lengths, and transposed keys (w << 32) | u with the
-// digit histograms of their `tpasses` low bytes of w.
+// A warp's DEDUP_ITEMS x 32 sorted forward keys from wbase (item i of lane l
+// is key wbase + 32 i + l; past the end, the sentinel), and per item the
+// ballot of the lanes holding the first key of a run of equal keys: the
+// unique forward edges. Returns how many the warp holds.
+__device__ __forceinline__ uint32_t load_unique(const uint64_t* __restrict__ keys, int64_t nkeys, uint64_t sentinel,
+                                                int64_t wbase, int lane, uint64_t (&k)[DEDUP_ITEMS],
+                                                uint32_t (&bal)[DEDUP_ITEMS]) {
+  uint64_t prev_last = ~0ULL;  // key just before this warp's first item
+  if (lane == 0 && wbase > 0 && wbase - 1 < nkeys) prev_last = keys[wbase - 1];
+  // all loads first, so their latencies overlap
+#pragma unroll
+  for (int i = 0; i < DEDUP_ITEMS; ++i) {
+    const int64_t idx = wbase + i * 32 + lane;
+    k[i] = idx < nkeys ? __ldcs(keys + idx) : sentinel;
+  }
+  uint32_t count = 0;
+#pragma unroll
+  for (int i = 0; i < DEDUP_ITEMS; ++i) {
+    const int64_t idx = wbase + i * 32 + lane;
+    const uint64_t up = __shfl_up_sync(FULL_MASK, k[i], 1);
+    const uint64_t from31 = __shfl_sync(FULL_MASK, k[i > 0 ? i - 1 : 0], 31);
+    const uint64_t prev = lane > 0 ? up : (i > 0 ? from31 : prev_last);
+    const bool f = (k[i] != sentinel) && (idx == 0 || k[i] != prev);
+    bal[i] = __ballot_sync(FULL_MASK, f);
+    count += __popc(bal[i]);
+  }
+  return count;
+}
+
+// Adjacent-unique of sorted forward keys (u, w): forward row lengths, the
+// transposed keys (w << 32) | u of the unique keys in order, with the digit
+// histograms of their `tpasses` low bytes of w, and per tile the number of
+// unique keys in earlier tiles (tile_excl), from which k_place_fwd later
+// recovers every unique key's index.
 __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restrict__ keys, int64_t nkeys, uint32_t b,
-                                                         int32_t n, uint64_t sentinel, uint64_t* __restrict__ fwd,
-                                                         uint64_t* __restrict__ tkeys, int tpasses,
-                                                         unsigned long long* __restrict__ thist,
-                                                         int32_t* __restrict__ fdeg, uint64_t* status,
-                                                         uint32_t* tile_ctr, uint32_t* err, int64_t* n_unique) {
+                                                         int32_t n, uint64_t sentinel, uint64_t* __restrict__ tkeys,
+                                                         int tpasses, unsigned long long* __restrict__ thist,
+                                                         int32_t* __restrict__ fdeg, uint64_t* __restrict__ tile_excl,
+                                                         uint64_t* status, uint32_t* tile_ctr, uint32_t* err,
+                                                         int64_t* n_unique) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_wcount[DEDUP_THREADS / 32];
   __shared__ uint64_t s_excl;
@@ -121,25 +154,7 @@ __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restr
 
   uint64_t k[DEDUP_ITEMS];
   uint32_t bal[DEDUP_ITEMS];
-  uint32_t wcount = 0;
-  uint64_t prev_last = ~0ULL;  // key just before this warp's first item
-  if (lane == 0 && wbase > 0 && wbase - 1 < nkeys) prev_last = keys[wbase - 1];
-  // all loads first, so their latencies overlap
-#pragma unroll
-  for (int i = 0; i < DEDUP_ITEMS; ++i) {
-    const int64_t idx = wbase + i * 32 + lane;
-    k[i] = idx < nkeys ? __ldcs(keys + idx) : sentinel;
-  }
-#pragma unroll
-  for (int i = 0; i < DEDUP_ITEMS; ++i) {
-    const int64_t idx = wbase + i * 32 + lane;
-    const uint64_t up = __shfl_up_sync(FULL_MASK, k[i], 1);
-    const uint64_t from31 = __shfl_sync(FULL_MASK, k[i > 0 ? i - 1 : 0], 31);
-    const uint64_t prev = lane > 0 ? up : (i > 0 ? from31 : prev_last);
-    const bool f = (k[i] != sentinel) && (idx == 0 || k[i] != prev);
-    bal[i] = __ballot_sync(FULL_MASK, f);
-    wcount += __popc(bal[i]);
-  }
+  const uint32_t wcount = load_unique(keys, nkeys, sentinel, wbase, lane, k, bal);
   if (lane == 0) s_wcount[warp] = wcount;
   __syncthreads();
   uint64_t tile_total = 0;
@@ -178,6 +193,7 @@ __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restr
     }
     if (lane == 0) {
       s_excl = excl;
+      tile_excl[tile] = excl;
       if ((tile + 1) * DEDUP_TILE >= nkeys) *n_unique = (int64_t)(excl + tile_total);
     }
   }
@@ -187,10 +203,8 @@ __global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restr
 #pragma unroll
   for (int i = 0; i < DEDUP_ITEMS; ++i) {
     if ((bal[i] >> lane) & 1u) {
-      const uint64_t at = pos + __popc(bal[i] & lt);
       const uint32_t w = (uint32_t)(k[i] & vmask);
-      fwd[at] = k[i];
-      tkeys[at] = ((uint64_t)w << 32) | (k[i] >> b);
+      tkeys[pos + __popc(bal[i] & lt)] = ((uint64_t)w << 32) | (k[i] >> b);
     }
     pos += __popc(bal[i]);
   }
@@ -239,24 +253,36 @@ __global__ __launch_bounds__(256) void k_rows(const int32_t* __restrict__ fdeg, 
   if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(maxdeg, mx);
 }
 
-// Forward entry i, key (u << b) | w, goes to i + boff[u + 1]: row u starts at
-// foff[u] + boff[u] and holds its boff[u + 1] - boff[u] backward entries first.
-// A warp places 128 consecutive entries per step, each lane four of them 32
-// apart, so every load and store instruction stays coalesced while four
-// loads per thread are in flight.
-__global__ __launch_bounds__(256) void k_place_fwd(const uint64_t* __restrict__ fwd, int64_t m, uint32_t b,
-                                                   const int64_t* __restrict__ boff, int32_t* __restrict__ adj) {
+// Forward entry i (the i-th unique sorted forward key (u << b) | w) goes to
+// i + boff[u + 1]: row u starts at foff[u] + boff[u] and holds its
+// boff[u + 1] - boff[u] backward entries first. The sorted keys are read
+// again tile by tile as k_dedup read them; tile_excl gives each tile's first
+// unique index, so the forward entries need no buffer of their own.
+__global__ __launch_bounds__(DEDUP_THREADS) void k_place_fwd(const uint64_t* __restrict__ keys, int64_t nkeys,
+                                                             uint32_t b, uint64_t sentinel,
+                                                             const uint64_t* __restrict__ tile_excl,
+                                                             const int64_t* __restrict__ boff,
+                                                             int32_t* __restrict__ adj) {
+  __shared__ uint32_t s_wcount[DEDUP_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t tile = blockIdx.x;
+  const int64_t wbase = tile * DEDUP_TILE + warp * (32 * DEDUP_ITEMS);
   const uint64_t vmask = (1ULL << b) - 1ULL;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane) * 4;  // this warp's first entry
-  const int64_t step = (int64_t)gridDim.x * blockDim.x * 4;
-  for (int64_t i0 = warp0 + lane; i0 < m; i0 += step) {
-    uint64_t k[4];
+  uint64_t k[DEDUP_ITEMS];
+  uint32_t bal[DEDUP_ITEMS];
+  const uint32_t wcount = load_unique(keys, nkeys, sentinel, wbase, lane, k, bal);
+  if (lane == 0) s_wcount[warp] = wcount;
+  __syncthreads();
+  uint64_t pos = tile_excl[tile];
+  for (int w = 0; w < warp; ++w) pos += s_wcount[w];
+  const uint32_t lt = lanemask_lt();
 #pragma unroll
-    for (int r = 0; r < 4; ++r) k[r] = i0 + 32 * r < m ? __ldcs(fwd + i0 + 32 * r) : 0ULL;
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-      if (i0 + 32 * r < m) adj[i0 + 32 * r + __ldg(boff + (k[r] >> b) + 1)] = (int32_t)(k[r] & vmask);
+  for (int i = 0; i < DEDUP_ITEMS; ++i) {
+    if ((bal[i] >> lane) & 1u) {
+      const uint64_t at = pos + __popc(bal[i] & lt);
+      adj[at + __ldg(boff + (k[i] >> b) + 1)] = (int32_t)(k[i] & vmask);
+    }
+    pos += __popc(bal[i]);
   }
 }
 
@@ -286,7 +312,8 @@ struct BuildBuffers {
   int32_t* dst_dev = nullptr;
   uint64_t* keys_a = nullptr;
   uint64_t* keys_b = nullptr;
-  uint64_t* fwd = nullptr;      // unique forward keys (u << b) | w
+  uint64_t* keys_c = nullptr;   // the transposed sort's second buffer
+  uint64_t* tile_excl = nullptr;  // unique forward keys before each dedup tile
   int32_t* fdeg = nullptr;      // forward then backward counts (2n)
   int64_t* foff = nullptr;      // their exclusive scans (2(n + 1))
   void* scratch = nullptr;
@@ -297,7 +324,8 @@ struct BuildBuffers {
     dfree(dst_dev, s);
     dfree(keys_a, s);
     dfree(keys_b, s);
-    dfree(fwd, s);
+    dfree(keys_c, s);
+    dfree(tile_excl, s);
     dfree(fdeg, s);
     dfree(foff, s);
     dfree(scratch, s);
@@ -424,12 +452,12 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
   BUILD_TRY(cudaMemsetAsync(g->deg, 0, (size_t)n_vertices * sizeof(int32_t), s), "wedge_graph_build");
 
   if (n_edges > 0) {
-    // keys_a / keys_b: forward keys and their sort buffer, then the
-    // transposed keys and theirs; fwd: unique forward keys; fdeg/bdeg and
+    // keys_a / keys_b: forward keys and their sort buffer (the sorted ones
+    // stay until the forward entries are placed), the other then holding the
+    // transposed keys, with keys_c as their sort buffer; fdeg/bdeg and
     // foff/boff: forward and backward counts and their exclusive scans.
     if ((st = dalloc_n(&bb.keys_a, (size_t)n_edges, s, "wedge_graph_build: keys")) != WEDGE_OK) return bail(st);
     if ((st = dalloc_n(&bb.keys_b, (size_t)n_edges, s, "wedge_graph_build: keys")) != WEDGE_OK) return bail(st);
-    if ((st = dalloc_n(&bb.fwd, (size_t)n_edges, s, "wedge_graph_build: rows")) != WEDGE_OK) return bail(st);
     if ((st = dalloc_n(&bb.fdeg, 2 * (size_t)n_vertices, s, "wedge_graph_build: rows")) != WEDGE_OK) return bail(st);
     if ((st = dalloc_n(&bb.foff, 2 * ((size_t)n_vertices + 1), s, "wedge_graph_build: rows")) != WEDGE_OK)
       return bail(st);
@@ -489,15 +517,16 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     // 3. unique forward entries, forward counts, transposed keys + their histograms
     const int tpasses = ((int)b + 7) / 8;
     const int64_t tiles = (n_edges + DEDUP_TILE - 1) / DEDUP_TILE;
+    if ((st = dalloc_n(&bb.tile_excl, (size_t)tiles, s, "wedge_graph_build: rows")) != WEDGE_OK) return bail(st);
     if ((st = sort_clear_hist(bb.scratch, s)) != WEDGE_OK) return bail(st);
     char* tail = static_cast<char*>(bb.scratch) + hist_bytes;  // past the histograms
     BUILD_TRY(cudaMemsetAsync(tail, 0, 256 + (size_t)tiles * sizeof(uint64_t), s), "wedge_graph_build");
     uint32_t* ctr = reinterpret_cast<uint32_t*>(tail);
     uint64_t* status = reinterpret_cast<uint64_t*>(tail + 256);
     st = launch("dedup_rows", s, [&] {
-      k_dedup<<<(unsigned)tiles, DEDUP_THREADS, 0, s>>>(sorted, n_edges, b, n_vertices, sentinel, bb.fwd, tkeys,
-                                                        tpasses, sort_hist_area(bb.scratch), bb.fdeg, status, ctr,
-                                                        bb.derr, bb.scalars);
+      k_dedup<<<(unsigned)tiles, DEDUP_THREADS, 0, s>>>(sorted, n_edges, b, n_vertices, sentinel, tkeys, tpasses,
+                                                        sort_hist_area(bb.scratch), bb.fdeg, bb.tile_excl, status,
+                                                        ctr, bb.derr, bb.scalars);
     });
     if (st != WEDGE_OK) return bail(st);
     int64_t m_unique = 0;
@@ -511,9 +540,10 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
                          static_cast<char*>(bb.scratch) + hist_bytes, bb.derr, s);
     if (st != WEDGE_OK) return bail(st);
     if (m_unique >= 2) {
+      if ((st = dalloc_n(&bb.keys_c, (size_t)m_unique, s, "wedge_graph_build: keys")) != WEDGE_OK) return bail(st);
       const SortEmit emit{g->adj, bb.foff, bdeg};
       uint64_t* unused = nullptr;
-      st = radix_sort_u64(tkeys, sorted, m_unique, (int)b, bb.scratch, bb.derr, s, &unused, true, 32, &emit);
+      st = radix_sort_u64(tkeys, bb.keys_c, m_unique, (int)b, bb.scratch, bb.derr, s, &unused, true, 32, &emit);
       if (st != WEDGE_OK) return bail(st);
     } else if (m_unique == 1) {  // one key is sorted already
       st = launch("place_rows", s, [&] {
@@ -534,9 +564,8 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     if (st != WEDGE_OK) return bail(st);
     if (m_unique > 0) {
       st = launch("place_rows", s, [&] {
-        const int64_t want = (m_unique / 4 + 255) / 256;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * 16));
-        k_place_fwd<<<grid, 256, 0, s>>>(bb.fwd, m_unique, b, boff, g->adj);
+        k_place_fwd<<<(unsigned)tiles, DEDUP_THREADS, 0, s>>>(sorted, n_edges, b, sentinel, bb.tile_excl, boff,
+                                                              g->adj);
       });
       if (st != WEDGE_OK) return bail(st);
     }
