@@ -66,6 +66,51 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t* status, int64_t til
   return excl;
 }
 
+// Same result as lookback(), reading the next W predecessors per round trip:
+// it consumes them in order, summing aggregates, up to the nearest inclusive
+// prefix (done) or the first word not yet published (polled again next
+// round). Walks of a dozen or more tiles, common when hundreds of tiles are
+// in flight, then cost a few round trips instead of one each. Bounded like
+// lookback(): SPIN_LIMIT rounds without progress record DERR_TIMEOUT and
+// return the partial sum, which never exceeds the true prefix.
+template <int W>
+__device__ __forceinline__ uint64_t lookback_window(const uint64_t* status, int64_t tile, int64_t stride,
+                                                    uint32_t epoch, uint32_t* err) {
+  uint64_t excl = 0;
+  int64_t j = tile - 1;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    uint64_t w[W];
+#pragma unroll
+    for (int r = 0; r < W; ++r) w[r] = j - r >= 0 ? ld_relaxed(status + (j - r) * stride) : lb_pack(epoch, LB_INC, 0);
+    int used = 0;
+    bool done = false, stop = false;
+#pragma unroll
+    for (int r = 0; r < W; ++r) {
+      if (!done && !stop) {
+        const uint64_t x = w[r];
+        if ((uint32_t)(x >> 60) != epoch || ((x >> 58) & 3ULL) == 0ULL) {
+          stop = true;
+        } else {
+          excl += x & LB_VALUE_MASK;
+          ++used;
+          done = ((x >> 58) & 3ULL) == LB_INC;
+        }
+      }
+    }
+    if (done) break;
+    if (used == 0) {
+      if (++spins >= SPIN_LIMIT) {
+        atomicOr(err, DERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(spins < 64 ? 32 : 256);
+    }
+    j -= used;
+  }
+  return excl;
+}
+
 // Warp-wide look-back over status words of stride 1 (call with all 32 lanes
 // of one warp). The nearest predecessor is polled alone; once it holds only
 // an aggregate, the lanes read 32 predecessors at once, so a chain of tiles

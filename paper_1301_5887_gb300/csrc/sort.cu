@@ -3,7 +3,7 @@
 // One-sweep scheme (Adinets and Merrill, "Onesweep: a faster least
 // significant digit radix sort for GPUs", 2022): one upfront pass builds the
 // 256-bin histograms of every digit position; each digit pass then reads and
-// writes the keys once. A 256-thread CTA counts its 4096-key tile's digits
+// writes the keys once. A 384-thread CTA counts its 6144-key tile's digits
 // per warp and publishes them for decoupled look-back before ranking, ranks
 // the keys stably with a warp-level multisplit (peer masks from digit-bit
 // ballots) straight into shared memory in digit order, and writes runs of
@@ -21,10 +21,11 @@ namespace {
 
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
-constexpr int SORT_THREADS = 256;
+constexpr int SORT_THREADS = 384;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
 constexpr int SORT_ITEMS = 16;
-constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 4096 keys
+constexpr int SORT_MIN_BLOCKS = 3;  // resident CTAs per SM the register budget must allow
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 6144 keys
 constexpr int MAX_PASSES = SORT_MAX_PASSES;
 constexpr int HIST_THREADS = 256;
 
@@ -143,21 +144,23 @@ __device__ __forceinline__ void rank_and_place(PassSmem& sm, const uint64_t (&k)
   }
 }
 
-// One LSD pass over a 4096-key tile:
+// One LSD pass over a 6144-key tile (three CTAs per SM; the 256 digit owners
+// are threads 0..255):
 //  1. load 16 keys per thread (coalesced) and count digits per warp;
 //  2. publish the tile's digit counts to the look-back words at once, so
 //     later tiles need not wait for this tile's ranking;
 //  3. rank keys stably within each warp (ballot-built peer masks; every
 //     peer reads the warp's position counter for its digit, the lowest peer
 //     advances it) and place them in shared memory in digit order;
-//  4. look back for the tile's global digit offsets;
+//  4. look back for the tile's global digit offsets (two predecessors per
+//     round trip);
 //  5. write runs of equal digits to their global positions.
 // HI: the pass's digit lies in the keys' high 32-bit half. EMIT (last pass
 // of a sort of transposed keys (w << 32) | u): instead of writing the key to
 // its sorted position j, write u to adj[j + emit.row_start[w]] and add the
 // runs of equal w to emit.count[w].
 template <bool HI, bool EMIT>
-__global__ __launch_bounds__(SORT_THREADS) void k_sort_pass(PassArgs a) {
+__global__ __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS) void k_sort_pass(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PassSmem& sm = *reinterpret_cast<PassSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -229,7 +232,7 @@ __global__ __launch_bounds__(SORT_THREADS) void k_sort_pass(PassArgs a) {
     if (tile == 0) {
       excl = a.base[tid];
     } else {
-      excl = lookback(a.status + tid, tile, RADIX, a.epoch, a.err);
+      excl = lookback_window<2>(a.status + tid, tile, RADIX, a.epoch, a.err);
     }
     // the tile count is the distance to the next digit's start
     const uint32_t next = tid + 1 < RADIX ? sm.dstart[tid + 1] : (uint32_t)nvalid;
