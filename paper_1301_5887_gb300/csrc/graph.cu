@@ -36,7 +36,7 @@
 namespace wedge {
 namespace {
 
-constexpr int DEDUP_THREADS = 256;
+constexpr int DEDUP_THREADS = 384;
 constexpr int DEDUP_ITEMS = 16;
 constexpr int DEDUP_TILE = DEDUP_THREADS * DEDUP_ITEMS;
 
@@ -134,7 +134,7 @@ __device__ __forceinline__ uint32_t load_unique(const uint64_t* __restrict__ key
 // histograms of their `tpasses` low bytes of w, and per tile the number of
 // unique keys in earlier tiles (tile_excl), from which k_place_fwd later
 // recovers every unique key's index.
-__global__ __launch_bounds__(DEDUP_THREADS) void k_dedup(const uint64_t* __restrict__ keys, int64_t nkeys, uint32_t b,
+__global__ __launch_bounds__(DEDUP_THREADS, 3) void k_dedup(const uint64_t* __restrict__ keys, int64_t nkeys, uint32_t b,
                                                          int32_t n, uint64_t sentinel, uint64_t* __restrict__ tkeys,
                                                          int tpasses, unsigned long long* __restrict__ thist,
                                                          int32_t* __restrict__ fdeg, uint64_t* __restrict__ tile_excl,
@@ -258,7 +258,7 @@ __global__ __launch_bounds__(256) void k_rows(const int32_t* __restrict__ fdeg, 
 // boff[u + 1] - boff[u] backward entries first. The sorted keys are read
 // again tile by tile as k_dedup read them; tile_excl gives each tile's first
 // unique index, so the forward entries need no buffer of their own.
-__global__ __launch_bounds__(DEDUP_THREADS) void k_place_fwd(const uint64_t* __restrict__ keys, int64_t nkeys,
+__global__ __launch_bounds__(DEDUP_THREADS, 3) void k_place_fwd(const uint64_t* __restrict__ keys, int64_t nkeys,
                                                              uint32_t b, uint64_t sentinel,
                                                              const uint64_t* __restrict__ tile_excl,
                                                              const int64_t* __restrict__ boff,
