@@ -217,8 +217,8 @@ ALG_BYTES = {
     "sort_onesweep_pass": lambda z: 16 * z["nkeys"],
     "sort_histogram": lambda z: 8 * z["nkeys"],
     "expand_edges": lambda z: 16 * z["n_edges"],
-    "dedup_rows": lambda z: 8 * z["n_edges"] + 8 * z["n_adj"],
-    "place_rows": lambda z: 6 * z["n_adj"],
+    "dedup_rows": lambda z: 8 * z["n_edges"] + 4 * z["n_adj"],  # keys in, transposed keys of the unique ones out
+    "place_rows": lambda z: 8 * z["n_edges"] + 2 * z["n_adj"],  # sorted keys in again, 4-byte entries out
     "row_offsets": lambda z: 36 * z["n"],
     "scan_degrees": lambda z: 12 * z["n"],
     "bin_count": lambda z: 4 * z["n"],
