@@ -8,9 +8,11 @@
 //   1. expand: each input pair (u, v), u != v, emits (min << b) | max;
 //      self-loops emit a sentinel that sorts last; ids outside [0, n) raise
 //      DERR_BAD_ID. The sort's digit histograms are accumulated as the keys
-//      appear. A host edge list streams through two device staging slots,
-//      its transfer overlapping the expansion of the previous chunk.
-//   2. sort: LSD radix over the 2b significant bits.
+//      appear.
+//   2. sort: LSD radix over the 2b significant bits. A host edge list lands
+//      in groups of at most an eighth of it; each group is expanded and
+//      sorted while the next one crosses the host link, and the sorted
+//      groups are merged pairwise.
 //   3. dedup: adjacent-unique keys (u, w), u < w, are the forward entries w
 //      of row u (one atomic per run of equal u per warp counts them); they
 //      become the transposed keys (w << 32) | u, compacted in order, whose
@@ -28,6 +30,7 @@
 //      which are still intact (the transposed sort ran in other buffers).
 #include <algorithm>
 #include <atomic>
+#include <vector>
 
 #include "device.cuh"
 #include "internal.h"
@@ -308,8 +311,6 @@ std::atomic<uint64_t> g_uid{1};
 
 struct BuildBuffers {
   cudaStream_t s;
-  int32_t* src_dev = nullptr;
-  int32_t* dst_dev = nullptr;
   uint64_t* keys_a = nullptr;
   uint64_t* keys_b = nullptr;
   uint64_t* keys_c = nullptr;   // the transposed sort's second buffer
@@ -320,8 +321,6 @@ struct BuildBuffers {
   uint32_t* derr = nullptr;     // [0] error bits, then padding
   int64_t* scalars = nullptr;   // [0] unique undirected edges, [1] max degree (int32 in low half)
   ~BuildBuffers() {
-    dfree(src_dev, s);
-    dfree(dst_dev, s);
     dfree(keys_a, s);
     dfree(keys_b, s);
     dfree(keys_c, s);
@@ -356,55 +355,53 @@ using namespace wedge;
     if (e__ != cudaSuccess) return bail(cuda_fail(e__, what)); \
   } while (0)
 
-// Edges per staging slot for host edge lists (two slots of two int32 arrays:
-// 512 MiB of device memory in all).
-constexpr int64_t STAGE_EDGES = int64_t(1) << 25;
+// Edges per sorted group of a host edge list: the least power of two, and
+// whole merge tiles, with at most eight groups.
+int64_t host_group_edges(int64_t n_edges) {
+  int64_t g = MERGE_RUN_MULTIPLE;
+  while (g * 8 < n_edges) g *= 2;
+  return g;
+}
 
-// Copy chunk after chunk of a host edge list into the two staging slots on a
-// side stream and expand each on s as soon as it has arrived; a slot is
-// refilled only after s has consumed its previous chunk.
-template <typename Expand>
-wedge_status stage_and_expand(const int32_t* src, const int32_t* dst, int64_t n_edges, int64_t chunk,
-                              int32_t* src_stage, int32_t* dst_stage, cudaStream_t s, Expand&& expand) {
+// Copy a host edge list group by group into device staging on a side stream
+// and hand each group to `group_work` on s as soon as it has landed, so the
+// work on one group overlaps the transfer of the next. The copies are issued
+// before the group's work, so a pageable copy that holds the host thread
+// still finds the previous group's work queued on s.
+template <typename GroupWork>
+wedge_status stage_groups(const int32_t* src, const int32_t* dst, int64_t n_edges, int64_t group,
+                          int32_t* src_stage, int32_t* dst_stage, cudaStream_t s, GroupWork&& group_work) {
+  const int64_t groups = (n_edges + group - 1) / group;
   cudaStream_t cs = nullptr;
-  cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> copied((size_t)groups, nullptr);
   auto finish = [&](wedge_status st) {
     // On failure s may not have waited for every copy: let them land before
-    // the caller frees the slots. Otherwise destroying a stream or event with
-    // work pending is deferred by CUDA until that work completes.
+    // the caller frees the staging. Otherwise destroying a stream or event
+    // with work pending is deferred by CUDA until that work completes.
     if (st != WEDGE_OK && cs) cudaStreamSynchronize(cs);
-    for (int i = 0; i < 2; ++i) {
-      if (copied[i]) cudaEventDestroy(copied[i]);
-      if (consumed[i]) cudaEventDestroy(consumed[i]);
-    }
+    for (cudaEvent_t ev : copied)
+      if (ev) cudaEventDestroy(ev);
     if (cs) cudaStreamDestroy(cs);
     return st;
   };
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+  for (size_t i = 0; i < copied.size() && e == cudaSuccess; ++i)
     e = cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&consumed[i], cudaEventDisableTiming);
-  }
-  // the copy stream starts after everything already queued on s
-  if (e == cudaSuccess) e = cudaEventRecord(consumed[0], s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, consumed[0], 0);
+  // the copy stream starts after everything already queued on s (the staging
+  // memory was allocated on s)
+  if (e == cudaSuccess) e = cudaEventRecord(copied[0], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, copied[0], 0);
   if (e != cudaSuccess) return finish(cuda_fail(e, "wedge_graph_build: staging"));
-  int64_t i = 0;
-  for (int64_t e0 = 0; e0 < n_edges; e0 += chunk, ++i) {
-    const int slot = (int)(i & 1);
-    const int64_t len = std::min(chunk, n_edges - e0);
-    int32_t* sd = src_stage + slot * chunk;
-    int32_t* dd = dst_stage + slot * chunk;
-    if (i >= 2) e = cudaStreamWaitEvent(cs, consumed[slot], 0);  // expansion of chunk i - 2 is done
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sd, src + e0, (size_t)len * 4, cudaMemcpyDefault, cs);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dd, dst + e0, (size_t)len * 4, cudaMemcpyDefault, cs);
-    if (e == cudaSuccess) e = cudaEventRecord(copied[slot], cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, copied[slot], 0);
+  for (int64_t i = 0; i < groups; ++i) {
+    const int64_t e0 = i * group;
+    const int64_t len = std::min(group, n_edges - e0);
+    e = cudaMemcpyAsync(src_stage + e0, src + e0, (size_t)len * 4, cudaMemcpyDefault, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst_stage + e0, dst + e0, (size_t)len * 4, cudaMemcpyDefault, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(copied[i], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, copied[i], 0);
     if (e != cudaSuccess) return finish(cuda_fail(e, "wedge_graph_build: staging"));
-    const wedge_status st = expand(sd, dd, e0, len);
+    const wedge_status st = group_work(e0, len);
     if (st != WEDGE_OK) return finish(st);
-    e = cudaEventRecord(consumed[slot], s);
-    if (e != cudaSuccess) return finish(cuda_fail(e, "wedge_graph_build: staging"));
   }
   return finish(WEDGE_OK);
 }
@@ -467,14 +464,13 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     // the transposed sort's histograms)
     const size_t hist_bytes = SORT_MAX_PASSES * 256 * sizeof(uint64_t);
     const size_t scratch_bytes =
-        std::max(sort_scratch_bytes(n_edges, 2 * (int)b),
+        std::max(std::max(sort_scratch_bytes(n_edges, 2 * (int)b), merge_scratch_bytes(n_edges)),
                  std::max(scan_scratch_bytes(n_edges), scan_scratch_bytes(n_vertices) + hist_bytes));
     if ((st = dalloc(&bb.scratch, scratch_bytes, s, "wedge_graph_build: scratch")) != WEDGE_OK) return bail(st);
     BUILD_TRY(cudaMemsetAsync(bb.fdeg, 0, 2 * (size_t)n_vertices * sizeof(int32_t), s), "wedge_graph_build");
 
-    // 1. forward keys, with the forward sort's digit histograms
+    // 1-2. forward keys, with the forward sort's digit histograms, and the sort
     const int passes = (2 * (int)b + 7) / 8;
-    if ((st = sort_clear_hist(bb.scratch, s)) != WEDGE_OK) return bail(st);
     auto expand = [&](const int32_t* s_in, const int32_t* d_in, int64_t e0, int64_t len) {
       uint64_t* k_out = bb.keys_a + e0;
       const bool vec = ((reinterpret_cast<uintptr_t>(s_in) | reinterpret_cast<uintptr_t>(d_in) |
@@ -491,27 +487,39 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
                                                sort_hist_area(bb.scratch), bb.derr);
       });
     };
-    if (device_accessible(src) && device_accessible(dst)) {
-      if ((st = expand(src, dst, 0, n_edges)) != WEDGE_OK) return bail(st);
-    } else {
-      // Host edge list: stream it through two staging slots. A copy stream
-      // fills slot i % 2 with chunk i while the caller's stream expands chunk
-      // i - 1, so the transfer over the host link overlaps the expansion.
-      const int64_t chunk = std::min<int64_t>(n_edges, STAGE_EDGES);
-      if ((st = dalloc_n(&bb.src_dev, 2 * (size_t)chunk, s, "wedge_graph_build: staging")) != WEDGE_OK) return bail(st);
-      if ((st = dalloc_n(&bb.dst_dev, 2 * (size_t)chunk, s, "wedge_graph_build: staging")) != WEDGE_OK) return bail(st);
-      if ((st = stage_and_expand(src, dst, n_edges, chunk, bb.src_dev, bb.dst_dev, s, expand)) != WEDGE_OK)
-        return bail(st);
-      // The staging slots go back to the pool once the last expansion is done.
-      dfree(bb.src_dev, s);
-      dfree(bb.dst_dev, s);
-      bb.src_dev = bb.dst_dev = nullptr;
-    }
-
-    // 2. forward sort
     uint64_t* sorted = nullptr;
-    st = radix_sort_u64(bb.keys_a, bb.keys_b, n_edges, 2 * (int)b, bb.scratch, bb.derr, s, &sorted, true);
-    if (st != WEDGE_OK) return bail(st);
+    if (device_accessible(src) && device_accessible(dst)) {
+      if ((st = sort_clear_hist(bb.scratch, s)) != WEDGE_OK) return bail(st);
+      if ((st = expand(src, dst, 0, n_edges)) != WEDGE_OK) return bail(st);
+      st = radix_sort_u64(bb.keys_a, bb.keys_b, n_edges, 2 * (int)b, bb.scratch, bb.derr, s, &sorted, true);
+      if (st != WEDGE_OK) return bail(st);
+    } else {
+      // Host edge list: it lands group by group in the adjacency buffer
+      // (2 n_edges int32, unused until the rows are placed: sources, then
+      // destinations), and each group is expanded and sorted on its own as
+      // soon as it has arrived, so the sorting overlaps the transfer over the
+      // host link; the sorted groups are then merged. Every group takes the
+      // same number of passes, so all of them end in the same buffer.
+      const int64_t group = host_group_edges(n_edges);
+      uint64_t* runs = (passes & 1) ? bb.keys_b : bb.keys_a;
+      auto group_work = [&](int64_t e0, int64_t len) {
+        wedge_status gst = sort_clear_hist(bb.scratch, s);
+        if (gst == WEDGE_OK) gst = expand(g->adj + e0, g->adj + n_edges + e0, e0, len);
+        uint64_t* gs = nullptr;
+        if (gst == WEDGE_OK)
+          gst = radix_sort_u64(bb.keys_a + e0, bb.keys_b + e0, len, 2 * (int)b, bb.scratch, bb.derr, s, &gs, true);
+        if (gst == WEDGE_OK && gs != runs + e0) {  // a one-key group is not moved by the sort
+          const cudaError_t ce = cudaMemcpyAsync(runs + e0, gs, (size_t)len * sizeof(uint64_t),
+                                                 cudaMemcpyDeviceToDevice, s);
+          if (ce != cudaSuccess) gst = cuda_fail(ce, "wedge_graph_build: group");
+        }
+        return gst;
+      };
+      if ((st = stage_groups(src, dst, n_edges, group, g->adj, g->adj + n_edges, s, group_work)) != WEDGE_OK)
+        return bail(st);
+      st = merge_sorted_runs(runs, runs == bb.keys_a ? bb.keys_b : bb.keys_a, n_edges, group, bb.scratch, s, &sorted);
+      if (st != WEDGE_OK) return bail(st);
+    }
     uint64_t* tkeys = sorted == bb.keys_a ? bb.keys_b : bb.keys_a;
 
     // 3. unique forward entries, forward counts, transposed keys + their histograms

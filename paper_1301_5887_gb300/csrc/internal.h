@@ -55,6 +55,15 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
                             cudaStream_t s, uint64_t** sorted, bool hist_ready, int shift0 = 0,
                             const SortEmit* emit = nullptr);
 
+// Merge of sorted runs (sort.cu): keys holds runs of `run` keys each (run a
+// multiple of MERGE_RUN_MULTIPLE; the last run may be shorter), each sorted;
+// pairwise merge passes ping-pong between keys and alt until one run is
+// left, and *merged points at it. scratch: merge_scratch_bytes(n).
+constexpr int64_t MERGE_RUN_MULTIPLE = 4096;
+size_t merge_scratch_bytes(int64_t n);
+wedge_status merge_sorted_runs(uint64_t* keys, uint64_t* alt, int64_t n, int64_t run, void* scratch, cudaStream_t s,
+                               uint64_t** merged);
+
 // Exclusive scans with decoupled look-back (scan.cu).
 size_t scan_scratch_bytes(int64_t n);
 // out[i] = sum in[0..i) for i < n; if total != nullptr, *total = sum of all.

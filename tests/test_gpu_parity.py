@@ -353,10 +353,12 @@ def test_maximum_vertex_ids():
 
 
 def test_host_input_streams_in_chunks():
-    """Host edge lists larger than one staging slot (2^25 edges) stream through
-    two slots; pinned and pageable host input give the device-input CSR bit for bit."""
+    """A host edge list crosses the link in groups of at most an eighth of it,
+    each sorted on its own, and the sorted groups are merged pairwise; pinned
+    and pageable host input give the device-input CSR bit for bit."""
     n = 1 << 22
-    hs, hd = graphgen.kronecker_host(22, n_edges=80_000_001, seed=5)  # 2 full chunks and a ragged one
+    m = 80_000_001  # groups of 2^24 edges: four full ones and a ragged fifth
+    hs, hd = graphgen.kronecker_host(22, n_edges=m, seed=5)
     ref = wedge.graph_build(torch.as_tensor(hs).cuda(), torch.as_tensor(hd).cuda(), n).csr_numpy()
     for src, dst in ((hs, hd), (torch.as_tensor(hs).pin_memory(), torch.as_tensor(hd).pin_memory())):
         got = wedge.graph_build(src, dst, n).csr_numpy()
@@ -365,7 +367,27 @@ def test_host_input_streams_in_chunks():
     wedge.profile_reset()
     wedge.profile_enable(False)
     wedge.graph_build(hs, hd, n)
-    assert wedge.profile_read()["expand_edges"]["launches"] == 3
+    prof = wedge.profile_read()
+    assert prof["expand_edges"]["launches"] == 5
+    assert prof["merge_runs"]["launches"] == 3  # 5 runs -> 3 -> 2 -> 1
+
+
+@pytest.mark.parametrize("m,n", [(4097, 700), (8193, 700), (32768, 700), (32769, 700), (40961, 200),
+                                 (65536 * 3 + 5, 700), (50000, 200)])
+def test_host_input_group_merge_boundaries(m, n):
+    """Two to eight groups, one-key and ragged last groups, unpaired runs in a
+    merge pass, odd and even sort pass counts (ids of 10 and 8 bits), and a
+    run of repeated keys across groups and merge tiles."""
+    rng = np.random.default_rng(m)
+    src = rng.integers(0, n, m).astype(np.int32)
+    dst = rng.integers(0, n, m).astype(np.int32)
+    src[: m // 4] = 3  # one long run of equal keys over several groups and tiles
+    dst[: m // 4] = 5
+    got = wedge.graph_build(src, dst, n).csr_numpy()
+    ref = wedge.graph_build(dev(src), dev(dst), n).csr_numpy()
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+    check_csr(wedge.graph_build(src, dst, n), src, dst, n)
 
 
 def test_profile_counts_launches():
