@@ -185,6 +185,7 @@ KERNEL_SOURCES = {
     "dedup_rows": ["graph.cu", "device.cuh"],
     "expand_edges": ["graph.cu"],
     "probe_random_read": ["probe.cu"],
+    "merge_runs": ["merge.cu"],
 }
 
 

@@ -55,7 +55,7 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
                             cudaStream_t s, uint64_t** sorted, bool hist_ready, int shift0 = 0,
                             const SortEmit* emit = nullptr);
 
-// Merge of sorted runs (sort.cu): keys holds runs of `run` keys each (run a
+// Merge of sorted runs (merge.cu): keys holds runs of `run` keys each (run a
 // multiple of MERGE_RUN_MULTIPLE; the last run may be shorter), each sorted;
 // pairwise merge passes ping-pong between keys and alt until one run is
 // left, and *merged points at it. scratch: merge_scratch_bytes(n).

@@ -281,146 +281,7 @@ __global__ __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS) void k_sort_pass(Pas
 
 int passes_for(int bits) { return (bits + RADIX_BITS - 1) / RADIX_BITS; }
 
-// Pairwise merge of sorted runs (merge path: Green, McColl and Bader, "GPU
-// merge path: a GPU merging algorithm", 2012). Runs of `run` keys (the last
-// one possibly shorter) are merged two by two into runs of 2 run keys; each
-// CTA writes one 4096-key tile of the output, and run is a multiple of the
-// tile, so no tile straddles two pairs.
-constexpr int MERGE_THREADS = 256;
-constexpr int MERGE_ITEMS = 16;
-constexpr int MERGE_TILE = MERGE_THREADS * MERGE_ITEMS;
-static_assert(MERGE_TILE == MERGE_RUN_MULTIPLE, "runs are whole merge tiles");
-
-// Keys of A among the first d outputs of merging sorted A[0, la) and
-// B[0, lb), ties going to A first.
-__device__ __forceinline__ int64_t merge_split(const uint64_t* A, int64_t la, const uint64_t* B, int64_t lb,
-                                               int64_t d) {
-  int64_t lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (A[mid] <= B[d - 1 - mid]) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
-// The pair an output position c falls in: its start P0 and run lengths.
-__device__ __forceinline__ void merge_pair(int64_t c, int64_t n, int64_t run, int64_t& p0, int64_t& la, int64_t& lb) {
-  p0 = c / (2 * run) * (2 * run);
-  la = n - p0 < run ? n - p0 : run;
-  const int64_t rest = n - p0 - la;
-  lb = rest < run ? rest : run;
-}
-
-// split[t] = the A-keys before output tile t's first position, within its pair.
-__global__ __launch_bounds__(256) void k_merge_partition(const uint64_t* __restrict__ in, int64_t n, int64_t run,
-                                                         int64_t tiles, int64_t* __restrict__ split) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= tiles) return;
-  const int64_t c0 = t * MERGE_TILE;
-  int64_t p0, la, lb;
-  merge_pair(c0, n, run, p0, la, lb);
-  split[t] = merge_split(in + p0, la, in + p0 + la, lb, c0 - p0);
-}
-
-// Shared-memory index of output position p: one padding word per 32 keys
-// spreads the threads' 16-key output runs over the banks. (Padding the
-// input side as well measured slower: the merge reads are not the limit.)
-__device__ __forceinline__ int merge_pad(int p) { return p + (p >> 5); }
-
-__global__ __launch_bounds__(MERGE_THREADS) void k_merge(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
-                                                         int64_t n, int64_t run, int64_t tiles,
-                                                         const int64_t* __restrict__ split) {
-  __shared__ uint64_t sk[MERGE_TILE + MERGE_TILE / 32];
-  const int tid = threadIdx.x;
-  const int64_t t = blockIdx.x;
-  const int64_t c0 = t * MERGE_TILE;
-  const int64_t c1 = c0 + MERGE_TILE < n ? c0 + MERGE_TILE : n;
-  int64_t p0, la, lb;
-  merge_pair(c0, n, run, p0, la, lb);
-  const int64_t i0 = split[t];
-  const int64_t i1 = (c1 - p0 == la + lb) ? la : split[t + 1];
-  const int64_t j0 = (c0 - p0) - i0, j1 = (c1 - p0) - i1;
-  const int na = (int)(i1 - i0), nb = (int)(j1 - j0), total = na + nb;
-  const uint64_t* A = in + p0 + i0;
-  const uint64_t* B = in + p0 + la + j0;
-  {
-    uint64_t v[MERGE_ITEMS];  // all loads first, so their latencies overlap
-#pragma unroll
-    for (int k = 0; k < MERGE_ITEMS; ++k) {
-      const int x = k * MERGE_THREADS + tid;
-      v[k] = x < na ? __ldcs(A + x) : (x < total ? __ldcs(B + (x - na)) : 0);
-    }
-#pragma unroll
-    for (int k = 0; k < MERGE_ITEMS; ++k) {
-      const int x = k * MERGE_THREADS + tid;
-      if (x < total) sk[x] = v[k];
-    }
-  }
-  __syncthreads();
-
-  // this thread's 16 outputs start at diagonal d of the tile's A | B
-  const int d = min(tid * MERGE_ITEMS, total);
-  int lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (sk[mid] <= sk[na + d - 1 - mid]) lo = mid + 1;
-    else hi = mid;
-  }
-  int ia = lo, ib = d - lo;
-  uint64_t a = ia < na ? sk[ia] : 0, bv = ib < nb ? sk[na + ib] : 0;
-  uint64_t r[MERGE_ITEMS];
-#pragma unroll
-  for (int k = 0; k < MERGE_ITEMS; ++k) {
-    const bool take_a = ia < na && (ib >= nb || a <= bv);
-    r[k] = take_a ? a : bv;
-    if (take_a) {
-      ++ia;
-      a = ia < na ? sk[ia] : 0;
-    } else {
-      ++ib;
-      bv = ib < nb ? sk[na + ib] : 0;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < MERGE_ITEMS; ++k)
-    if (d + k < total) sk[merge_pad(d + k)] = r[k];
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < MERGE_ITEMS; ++k) {
-    const int x = k * MERGE_THREADS + tid;
-    if (x < total) __stcs(out + c0 + x, sk[merge_pad(x)]);
-  }
-}
-
 }  // namespace
-
-size_t merge_scratch_bytes(int64_t n) { return (size_t)((n + MERGE_TILE - 1) / MERGE_TILE + 1) * sizeof(int64_t); }
-
-wedge_status merge_sorted_runs(uint64_t* keys, uint64_t* alt, int64_t n, int64_t run, void* scratch, cudaStream_t s,
-                               uint64_t** merged) {
-  *merged = keys;
-  if (run < 1 || run % MERGE_TILE) return fail(WEDGE_EINVAL, "merge: run length %lld", (long long)run);
-  const int64_t tiles = (n + MERGE_TILE - 1) / MERGE_TILE;
-  if (tiles > (int64_t)INT32_MAX) return fail(WEDGE_EINVAL, "merge: too many keys (%lld)", (long long)n);
-  int64_t* split = static_cast<int64_t*>(scratch);
-  uint64_t* src = keys;
-  uint64_t* dst = alt;
-  for (; run < n; run *= 2) {
-    wedge_status st = launch("merge_partition", s, [&] {
-      k_merge_partition<<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(src, n, run, tiles, split);
-    });
-    if (st != WEDGE_OK) return st;
-    st = launch("merge_runs", s, [&] { k_merge<<<(unsigned)tiles, MERGE_THREADS, 0, s>>>(src, dst, n, run, tiles, split); });
-    if (st != WEDGE_OK) return st;
-    uint64_t* t = src;
-    src = dst;
-    dst = t;
-  }
-  *merged = src;
-  return WEDGE_OK;
-}
 
 // Scratch: [hist 8*256 u64][base 8*256 u64][counters 256 B][status tiles*256 u64]
 size_t sort_scratch_bytes(int64_t n, int bits) {
