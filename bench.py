@@ -573,7 +573,8 @@ def run_ours(args):
         gi, bi = g.info(), b.info()
         info.update(n_adj=gi.n_adj, n2=bi.n_wedge_vertices, n_bins=bi.n_bins,
                     samples=int(c.k_b.sum()) + c.k_global, c_hat=est["c_hat"], c_hat_global=est["c_hat_global"],
-                    n_streams=int((c.k_b > 0).sum()) + (1 if c.k_global else 0))
+                    n_streams=int((c.k_b > 0).sum()) + (1 if c.k_global else 0),
+                    counts=(c.q.tobytes(), c.k_b.tobytes(), c.k_global, c.closed_global, gi.n_adj))
         b.free()
         g.free()
 
@@ -670,8 +671,11 @@ def run_ours(args):
         l1.record(stream)
         torch.cuda.synchronize()
         link_gbs = 8 * n_edges / (l0.elapsed_time(l1) / 1e3) / 1e9
+        device_counts = info["counts"]
         step(hsrc, hdst)  # warm the staging path
         torch.cuda.synchronize()
+        # the grouped host path must give the device path's graph and samples
+        same_as_device = info["counts"] == device_counts
         times = []
         for _ in range(args.e2e_steps):
             if world > 1:
@@ -688,7 +692,7 @@ def run_ours(args):
         d2h = 8 + 16 + 2 * 8 * info["n_bins"] + 4 + 8 * (4 * info["n_streams"] + 34 * 34)
         e2e = {"value": dt / (world * m / 1e6), "unit": "s/Medge", "h2d_bytes_per_step": 8 * n_edges,
                "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "step_ms": [x * 1e3 for x in times],
-               "h2d_link_gbs": link_gbs}
+               "h2d_link_gbs": link_gbs, "counts_identical_to_device_input": same_as_device}
         del hsrc, hdst
 
     # Triangle statistics (Sec. 5.7): k global-stream samples, closed ones
