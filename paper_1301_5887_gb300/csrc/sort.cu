@@ -99,14 +99,15 @@ constexpr size_t PASS_SMEM = sizeof(PassSmem);
 // the warp holding the same value. One ballot per digit bit (plus one for the
 // no-key marker unless every lane holds a key), all issued first; a lane
 // differs from this one where a ballot disagrees with this lane's bit.
-template <bool FULL>
+// RB: the digit's significant bits (the rest are zero in every key).
+template <bool FULL, int RB>
 __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
-  uint32_t m[RADIX_BITS];
+  uint32_t m[RB];
 #pragma unroll
-  for (int b = 0; b < RADIX_BITS; ++b) m[b] = __ballot_sync(FULL_MASK, (d >> b) & 1u);
+  for (int b = 0; b < RB; ++b) m[b] = __ballot_sync(FULL_MASK, (d >> b) & 1u);
   uint32_t differ = 0;
 #pragma unroll
-  for (int b = 0; b < RADIX_BITS; ++b) differ |= m[b] ^ (0u - ((d >> b) & 1u));
+  for (int b = 0; b < RB; ++b) differ |= m[b] ^ (0u - ((d >> b) & 1u));
   if (!FULL) differ |= __ballot_sync(FULL_MASK, d >> RADIX_BITS) ^ (0u - (d >> RADIX_BITS));
   return ~differ;
 }
@@ -123,7 +124,7 @@ __device__ __forceinline__ uint32_t digit_of(uint64_t k, uint32_t sel) {
 // the tile position of this warp's next key of digit d: every peer reads it,
 // the lowest peer advances it past the group, and each key lands at that
 // position plus the number of its peers in lower lanes.
-template <bool HI, bool FULL>
+template <bool HI, bool FULL, int RB>
 __device__ __forceinline__ void rank_and_place(PassSmem& sm, const uint64_t (&k)[SORT_ITEMS], uint32_t sel,
                                                int nvalid, int warp, int lane) {
   const uint32_t lt = lanemask_lt();
@@ -132,7 +133,7 @@ __device__ __forceinline__ void rank_and_place(PassSmem& sm, const uint64_t (&k)
     const int li = warp * (32 * SORT_ITEMS) + i * 32 + lane;
     const bool has = FULL || li < nvalid;
     const uint32_t d = has ? digit_of<HI>(k[i], sel) : (uint32_t)RADIX;
-    const uint32_t peers = digit_peers<FULL>(d);
+    const uint32_t peers = digit_peers<FULL, RB>(d);
     const uint32_t below = peers & lt;
     const uint32_t next = has ? sm.whist[warp][d] : 0u;
     __syncwarp();  // every peer has read the counter before the lowest one moves it
@@ -158,8 +159,9 @@ __device__ __forceinline__ void rank_and_place(PassSmem& sm, const uint64_t (&k)
 // HI: the pass's digit lies in the keys' high 32-bit half. EMIT (last pass
 // of a sort of transposed keys (w << 32) | u): instead of writing the key to
 // its sorted position j, write u to adj[j + emit.row_start[w]] and add the
-// runs of equal w to emit.count[w].
-template <bool HI, bool EMIT>
+// runs of equal w to emit.count[w]. RB < 8: only the digit's low RB bits can
+// be nonzero in any key (the top digit of keys narrower than the passes).
+template <bool HI, bool EMIT, int RB = RADIX_BITS>
 __global__ __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS) void k_sort_pass(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PassSmem& sm = *reinterpret_cast<PassSmem*>(smem_raw);
@@ -222,8 +224,8 @@ __global__ __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS) void k_sort_pass(Pas
   __syncthreads();
 
   // 3. stable warp-level rank, scattered into shared memory in digit order
-  if (nvalid == SORT_TILE) rank_and_place<HI, true>(sm, k, sel, nvalid, warp, lane);
-  else rank_and_place<HI, false>(sm, k, sel, nvalid, warp, lane);
+  if (nvalid == SORT_TILE) rank_and_place<HI, true, RB>(sm, k, sel, nvalid, warp, lane);
+  else rank_and_place<HI, false, RB>(sm, k, sel, nvalid, warp, lane);
 
   // 4. look-back for the global offset of each digit
   __syncthreads();
@@ -339,6 +341,9 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
     WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)PASS_SMEM),
                    "radix sort: shared memory");
+    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass<true, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)PASS_SMEM),
+                   "radix sort: shared memory");
     attr_set = true;
   }
   if (emit && shift0 < 32) return fail(WEDGE_EINVAL, "radix sort: placement needs keys sorted from bit 32");
@@ -357,8 +362,12 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
     a.err = derr;
     a.emit = emit ? *emit : SortEmit{};
     const bool place = emit && p == passes - 1;
+    // the placing pass's digit is the top of w: with at most 4 of its bits
+    // in use (b = 28: bits 24..27), the rank looks at those 4 alone
+    const bool narrow = bits - RADIX_BITS * (passes - 1) <= 4;
     st = launch("sort_onesweep_pass", s, [&] {
-      if (place) k_sort_pass<true, true><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
+      if (place && narrow) k_sort_pass<true, true, 4><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
+      else if (place) k_sort_pass<true, true><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
       else if (a.shift >= 32) k_sort_pass<true, false><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
       else k_sort_pass<false, false><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
     });
