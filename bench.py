@@ -672,7 +672,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         link_gbs = 8 * n_edges / (l0.elapsed_time(l1) / 1e3) / 1e9
         device_counts = info["counts"]
-        step(hsrc, hdst)  # warm the staging path
+        step(hsrc, hdst)  # warm the host-input path
         torch.cuda.synchronize()
         # the grouped host path must give the device path's graph and samples
         same_as_device = info["counts"] == device_counts

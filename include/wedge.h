@@ -78,7 +78,10 @@ WEDGE_API int wedge_abi_sizes(uint64_t* sizes, int cap);
  * in [0, n_vertices). The graph is undirected: {u,v} is an edge iff u != v and
  * (u,v) or (v,u) appears; repeated pairs collapse and self-loops are dropped.
  * src and dst are host or device int32 arrays of n_edges entries, read before
- * the call returns. Output: *out, a graph whose adjacency rows are sorted
+ * the call returns. A host list crosses the link in groups of at most an
+ * eighth of it, each sorted on the device while the next is copied (pinned
+ * host memory lets the copies run asynchronously); the result is the same as
+ * for device input. Output: *out, a graph whose adjacency rows are sorted
  * ascending (degree d_v = row length, Alg. Phase 1a).
  * Errors: EINVAL if n_edges < 0, n_vertices < 1, n_vertices > 2^31 - 1, a
  * pointer is NULL while n_edges > 0, or an id is outside [0, n_vertices);

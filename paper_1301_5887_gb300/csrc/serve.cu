@@ -78,7 +78,7 @@ uint64_t graph_bytes_estimate(int64_t n_edges, int32_t n) {
   return 8 * (uint64_t)(n_edges > 0 ? n_edges : 1) + 24 * (uint64_t)n + 16;
 }
 
-// Build scratch of wedge_graph_build: two key buffers, look-back words and staging.
+// Build scratch of wedge_graph_build: key buffers and look-back words.
 uint64_t build_scratch_bytes(int64_t n_edges, int32_t n) {
   const uint64_t keys = 2 * (uint64_t)n_edges;
   return 2 * 8 * keys + keys / 16 + 8 * (uint64_t)n_edges + 16 * (uint64_t)n;
