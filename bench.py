@@ -189,6 +189,18 @@ KERNEL_SOURCES = {
 }
 
 
+def host_available_bytes():
+    """MemAvailable from /proc/meminfo, or None where it cannot be read."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
 def source_hash(kernel):
     import hashlib
     h = hashlib.sha256()
@@ -654,7 +666,24 @@ def run_ours(args):
     # e2e: the same step from pinned host buffers through the C ABI, each step
     # timed on its own (the host link is shared with the node's other tenants).
     e2e = None
-    if args.e2e_steps > 0:
+    e2e_room = args.e2e_steps > 0
+    if e2e_room:
+        # Every rank on this node pins its own copy of the edge list: where the
+        # node's free host memory cannot hold them all, the leg is skipped and
+        # the line says why (all ranks take the same decision).
+        local_world = int(os.environ.get("LOCAL_WORLD_SIZE", str(world)))
+        need = local_world * 8 * n_edges
+        avail = host_available_bytes()
+        e2e_room = avail is None or need <= 0.8 * avail
+        if world > 1:
+            flag = torch.tensor([1 if e2e_room else 0], device="cuda", dtype=torch.int32)
+            dist.all_reduce(flag, op=dist.ReduceOp.MIN)
+            e2e_room = bool(flag.item())
+        if not e2e_room:
+            e2e = {"value": None, "unit": "s/Medge", "h2d_bytes_per_step": 8 * n_edges, "d2h_bytes_per_step": None,
+                   "skipped": f"host memory: {local_world} rank(s) need {need / 1e9:.1f} GB of pinned edge lists, "
+                              f"{(avail or 0) / 1e9:.1f} GB available"}
+    if e2e_room:
         hsrc = torch.empty(n_edges, dtype=torch.int32, pin_memory=True)
         hdst = torch.empty(n_edges, dtype=torch.int32, pin_memory=True)
         hsrc.copy_(src)
@@ -766,7 +795,7 @@ def run_ours(args):
                 "gwedges_checked_per_s": gwps, "sampling_ms": samp_ms,
                 "s_per_M_generated_edges": {"device": (ms_step / 1e3) / (world * n_edges / 1e6),
                                             "e2e": (e2e["ms_per_step"] / 1e3) / (world * n_edges / 1e6)
-                                            if e2e else None}, "batched": batched, "serving": serving,
+                                            if e2e and e2e.get("ms_per_step") else None}, "batched": batched, "serving": serving,
                 "triangle_stats": tri, "rounding": rounding, "sorted_closure": sorted_cl, "roofline": roofline, "sampling_roofline": sampling_roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
                 "clocks": clk, "kernels": kernels,
                 "estimates": {"c_hat": info["c_hat"], "c_hat_global": info["c_hat_global"]}}
