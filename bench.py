@@ -184,6 +184,7 @@ KERNEL_SOURCES = {
     "sample_closure": ["sample.cu", "sample_device.cuh", "device.cuh"],
     "dedup_rows": ["graph.cu", "device.cuh"],
     "expand_edges": ["graph.cu"],
+    "edge_histograms": ["graph.cu"],
     "probe_random_read": ["probe.cu"],
     "merge_runs": ["merge.cu"],
 }
@@ -224,11 +225,15 @@ def ncu_figures(kernel):
 
 
 ALG_BYTES = {
-    # algorithmic DRAM bytes per launch, from the sizes of one step. "nkeys" is
-    # the mean keys per sort pass: 2b-bit forward keys (one per edge) and b-bit
-    # transposed keys (one per unique edge, m = n_adj / 2)
-    "sort_onesweep_pass": lambda z: 16 * z["nkeys"],
+    # algorithmic DRAM bytes per launch, from the sizes of one step.
+    # sort_onesweep_pass: the mean over the step's passes of 16 B per key
+    # (8 read + 8 written) for the forward passes (one key per generated edge;
+    # the first reads the edge's two int32 endpoints) and the transposed ones
+    # (one key per unique edge, m = n_adj / 2), except the last transposed pass,
+    # which reads 8 B and writes one 4 B adjacency entry per key
+    "sort_onesweep_pass": lambda z: z["sort_bytes"] / z["sort_launches"],
     "sort_histogram": lambda z: 8 * z["nkeys"],
+    "edge_histograms": lambda z: 8 * z["n_edges"],
     "expand_edges": lambda z: 16 * z["n_edges"],
     "dedup_rows": lambda z: 8 * z["n_edges"] + 4 * z["n_adj"],  # keys in, transposed keys of the unique ones out
     "place_rows": lambda z: 8 * z["n_edges"] + 2 * z["n_adj"],  # sorted keys in again, 4-byte entries out
@@ -241,10 +246,13 @@ ALG_BYTES = {
 
 
 def sort_sizes(n_edges, n_adj, id_bits):
-    """Mean keys per sort pass: ceil(2b/8) passes over the forward keys, then
-    ceil(b/8) over the transposed ones."""
+    """Sort passes of one CSR build: ceil(2b/8) over the forward keys, then
+    ceil(b/8) over the transposed ones. Returns (mean keys per pass, passes,
+    algorithmic bytes of all passes)."""
     pf, pt = (2 * id_bits + 7) // 8, (id_bits + 7) // 8
-    return (pf * n_edges + pt * (n_adj // 2)) / (pf + pt)
+    m = n_adj // 2
+    nbytes = 16 * pf * n_edges + 16 * (pt - 1) * m + 12 * m
+    return (pf * n_edges + pt * m) / (pf + pt), pf + pt, nbytes
 
 
 def build_batched_mix(wedge, graphgen, torch, n_graphs=512, seed=3):
@@ -626,8 +634,9 @@ def run_ours(args):
     gwps = world * info["samples"] / (samp_ms / 1e3) / 1e9 if samp_ms > 0 else None
     launches = sum(v["launches"] for v in prof.values())
 
-    sizes = {"nkeys": sort_sizes(n_edges, info["n_adj"], scale), "n_edges": n_edges, "n_adj": info["n_adj"], "n": n,
-             "n2": info["n2"]}
+    nkeys, sort_launches, sort_bytes = sort_sizes(n_edges, info["n_adj"], scale)
+    sizes = {"nkeys": nkeys, "sort_launches": sort_launches, "sort_bytes": sort_bytes, "n_edges": n_edges,
+             "n_adj": info["n_adj"], "n": n, "n2": info["n2"]}
     top = max((k for k in prof if k in ALG_BYTES), key=lambda k: prof[k]["total_ms"])
     peaks, peak_kind = measured_peaks()
     avg_ms = prof[top]["total_ms"] / prof[top]["launches"]

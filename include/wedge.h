@@ -518,17 +518,23 @@ WEDGE_API wedge_status wedge_triangle_stats(const wedge_graph* g, const wedge_bi
  * off[n] is the total), with the same single-pass scan kernel, but keeps the
  * kernel's look-back scratch in a fixed 1 MiB device array inside the
  * library instead of allocating it.
- *   deg: device, n int32 degrees (>= 0); off: device, n + 1 int64 outputs.
+ *   deg: device, n int32 degrees, each >= 0, whose total is below 2^58;
+ *   off: device, n + 1 int64 outputs (the caller owns both).
  *   Returns after synchronising s. Allocates no device memory and calls no
  *   allocating routine.
  *   The scratch array is resident on every GPU that loads the library until
  *   the process exits. The first call on a device looks up the array's device
- *   address; make that first call before any stream capture on that device.
+ *   address (a runtime query, cudaGetSymbolAddress) and keeps it for the rest
+ *   of the process; make that first call before any stream capture on that
+ *   device, so that the query does not run while a capture is in progress.
+ *   The kept address belongs to the device's current context: do not call
+ *   this entry point on a device after cudaDeviceReset().
  *   All calls share the one array, so calls that overlap on the GPU (other
  *   host threads, other streams) race and must be serialised by the caller.
- *   Errors: EINVAL if n < 0, a pointer is NULL, or n exceeds
- *   WEDGE_NOALLOC_MAX_VERTICES; ECUDA; ETIMEOUT (a bounded look-back wait
- *   gave up).
+ *   Errors: EINVAL if n < 0, a pointer is NULL, n exceeds
+ *   WEDGE_NOALLOC_MAX_VERTICES or a degree is negative; EOVERFLOW if the
+ *   degree total reaches 2^58; ECUDA; ETIMEOUT (a bounded look-back wait gave
+ *   up). On EINVAL or EOVERFLOW from the device checks, off is unspecified.
  * ------------------------------------------------------------------------ */
 #define WEDGE_NOALLOC_MAX_VERTICES 536870912LL /* 131072 tiles x 4096 degrees */
 WEDGE_API wedge_status wedge_degree_offsets_noalloc(const int32_t* deg, int64_t n, int64_t* off, wedge_stream s);

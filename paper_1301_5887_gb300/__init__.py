@@ -490,11 +490,24 @@ NOALLOC_MAX_VERTICES = 536870912
 
 def degree_offsets_noalloc(deg, off, stream=None):
     """Row offsets off[0..n] from device degrees deg[0..n) without any device
-    allocation (wedge_degree_offsets_noalloc); off must hold n + 1 int64."""
+    allocation (wedge_degree_offsets_noalloc). deg: contiguous int32 CUDA
+    tensor; off: contiguous int64 CUDA tensor of at least n + 1 entries, on
+    the same (current) device, written in place."""
+    import torch
     lib = load()
-    pd, kd = _ptr(deg, np.int32)
-    po, _ = _ptr(off, np.int64)
-    _check(lib.wedge_degree_offsets_noalloc(pd, int(kd.shape[0]), po, _stream_handle(stream)))
+    for name, t, dt in (("deg", deg, torch.int32), ("off", off, torch.int64)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must be on the current CUDA device")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous (off is written in place)")
+    n = deg.numel()
+    if off.numel() < n + 1:
+        raise ValueError(f"off holds {off.numel()} entries; n + 1 = {n + 1} are needed")
+    _check(lib.wedge_degree_offsets_noalloc(deg.data_ptr(), n, off.data_ptr(), _stream_handle(stream)))
 
 
 def hoeffding_k(eps: float, delta: float) -> int:

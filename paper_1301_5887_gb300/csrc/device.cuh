@@ -12,6 +12,7 @@ constexpr unsigned FULL_MASK = 0xffffffffu;
 constexpr uint32_t DERR_BAD_ID = 1u;     // an input id outside [0, n)
 constexpr uint32_t DERR_TIMEOUT = 2u;    // a look-back wait gave up
 constexpr uint32_t DERR_OVERFLOW = 4u;   // a count overflowed
+constexpr uint32_t DERR_NEGATIVE = 8u;   // a count that must be >= 0 was negative
 
 // A look-back wait polls at most this many times (with nanosleep back-off,
 // about a second) before it records DERR_TIMEOUT and stops waiting.
@@ -214,6 +215,21 @@ __device__ __forceinline__ uint32_t bin_of(const BinTable& t, uint64_t d) {
     if (t.lo[mid] <= d) lo = mid; else hi = mid;
   }
   return lo;
+}
+
+// --------------------------------------------------------------------------
+// CSR build: packed forward key of input pair (u, v): (min << b) | max, or
+// the sentinel for a self-loop or an id outside [0, n) (the latter raising
+// DERR_BAD_ID).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t edge_key(int32_t u, int32_t v, int32_t n, uint32_t b, uint64_t sentinel,
+                                             uint32_t* err) {
+  if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
+    atomicOr(err, DERR_BAD_ID);
+    return sentinel;
+  }
+  if (u == v) return sentinel;
+  return u < v ? ((uint64_t)u << b) | (uint64_t)v : ((uint64_t)v << b) | (uint64_t)u;
 }
 
 // BinId with tau = 2, omega = 2 (closed-wedge statistics, Sec. 5.7):

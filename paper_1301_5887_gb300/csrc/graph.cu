@@ -5,14 +5,16 @@
 // key (min << b) | max; the other direction comes from the deduplicated
 // edges, whose transposed keys are already ordered by the smaller endpoint,
 // so a stable sort on the larger endpoint's bits alone orders them fully:
-//   1. expand: each input pair (u, v), u != v, emits (min << b) | max;
-//      self-loops emit a sentinel that sorts last; ids outside [0, n) raise
-//      DERR_BAD_ID. The sort's digit histograms are accumulated as the keys
-//      appear.
-//   2. sort: LSD radix over the 2b significant bits. A host edge list lands
-//      in groups of at most an eighth of it; each group is expanded and
-//      sorted while the next one crosses the host link, and the sorted
-//      groups are merged pairwise.
+//   1. keys: each input pair (u, v), u != v, stands for the key
+//      (min << b) | max; self-loops for a sentinel that sorts last; ids
+//      outside [0, n) raise DERR_BAD_ID. One streaming pass over the edges
+//      builds the sort's digit histograms.
+//   2. sort: LSD radix over the 2b significant bits; the first pass computes
+//      the keys from the edges as it loads them (its input order carries no
+//      meaning, so it ranks without stability), so the keys are never
+//      written out unsorted. A host edge list lands in groups of at most an
+//      eighth of it; each group is sorted while the next one crosses the host
+//      link, and the sorted groups are merged pairwise.
 //   3. dedup: adjacent-unique keys (u, w), u < w, are the forward entries w
 //      of row u (one atomic per run of equal u per warp counts them); they
 //      become the transposed keys (w << 32) | u, compacted in order, whose
@@ -43,18 +45,6 @@ constexpr int DEDUP_THREADS = 384;
 constexpr int DEDUP_ITEMS = 16;
 constexpr int DEDUP_TILE = DEDUP_THREADS * DEDUP_ITEMS;
 
-// Packed forward key of input pair (u, v): (min << b) | max, or the sentinel
-// for a self-loop or an id outside [0, n) (the latter raising DERR_BAD_ID).
-__device__ __forceinline__ uint64_t edge_key(int32_t u, int32_t v, int32_t n, uint32_t b, uint64_t sentinel,
-                                             uint32_t* err) {
-  if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
-    atomicOr(err, DERR_BAD_ID);
-    return sentinel;
-  }
-  if (u == v) return sentinel;
-  return u < v ? ((uint64_t)u << b) | (uint64_t)v : ((uint64_t)v << b) | (uint64_t)u;
-}
-
 __device__ __forceinline__ void count_digits(uint32_t* sh, uint64_t key, int passes) {
   for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + (uint32_t)((key >> (8 * p)) & 255u)], 1u);
 }
@@ -63,8 +53,9 @@ __device__ __forceinline__ void count_digits(uint32_t* sh, uint64_t key, int pas
 // histograms (8-bit digits, `passes` of them) in shared memory on the way.
 // VEC: src, dst and keys are 16-byte aligned, and each thread takes four
 // edges per step with 16-byte loads (the scalar form keeps too few bytes in
-// flight to stream at the HBM rate).
-template <bool VEC>
+// flight to stream at the HBM rate). WRITE false: histograms only (the sort's
+// first pass then computes the keys from the edges itself).
+template <bool VEC, bool WRITE>
 __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                                                 int64_t m, int32_t n, uint32_t b, uint64_t sentinel, int passes,
                                                 uint64_t* __restrict__ keys, unsigned long long* __restrict__ hist,
@@ -84,8 +75,10 @@ __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src,
       const int4 u = __ldcs(s4 + e), v = __ldcs(d4 + e);
       const uint64_t k0 = edge_key(u.x, v.x, n, b, sentinel, err), k1 = edge_key(u.y, v.y, n, b, sentinel, err);
       const uint64_t k2v = edge_key(u.z, v.z, n, b, sentinel, err), k3 = edge_key(u.w, v.w, n, b, sentinel, err);
-      __stcs(k2 + 2 * e, make_ulonglong2(k0, k1));
-      __stcs(k2 + 2 * e + 1, make_ulonglong2(k2v, k3));
+      if (WRITE) {
+        __stcs(k2 + 2 * e, make_ulonglong2(k0, k1));
+        __stcs(k2 + 2 * e + 1, make_ulonglong2(k2v, k3));
+      }
       count_digits(sh, k0, passes);
       count_digits(sh, k1, passes);
       count_digits(sh, k2v, passes);
@@ -95,7 +88,7 @@ __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src,
   }
   for (int64_t e = scalar_from + t0; e < m; e += stride) {
     const uint64_t key = edge_key(__ldcs(src + e), __ldcs(dst + e), n, b, sentinel, err);
-    __stcs(keys + e, key);
+    if (WRITE) __stcs(keys + e, key);
     count_digits(sh, key, passes);
   }
   __syncthreads();
@@ -469,30 +462,46 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     if ((st = dalloc(&bb.scratch, scratch_bytes, s, "wedge_graph_build: scratch")) != WEDGE_OK) return bail(st);
     BUILD_TRY(cudaMemsetAsync(bb.fdeg, 0, 2 * (size_t)n_vertices * sizeof(int32_t), s), "wedge_graph_build");
 
-    // 1-2. forward keys, with the forward sort's digit histograms, and the sort
+    // 1-2. the forward sort's digit histograms, then the sort, whose first
+    //     pass computes the forward keys from the edges (a one-edge list is
+    //     expanded into keys instead)
     const int passes = (2 * (int)b + 7) / 8;
-    auto expand = [&](const int32_t* s_in, const int32_t* d_in, int64_t e0, int64_t len) {
+    auto expand = [&](const int32_t* s_in, const int32_t* d_in, int64_t e0, int64_t len, bool write) {
       uint64_t* k_out = bb.keys_a + e0;
       const bool vec = ((reinterpret_cast<uintptr_t>(s_in) | reinterpret_cast<uintptr_t>(d_in) |
                          reinterpret_cast<uintptr_t>(k_out)) & 15) == 0;
       // twice the usual grid: more resident loads in flight
       const int64_t units = vec ? (len + 3) / 4 : len;
       const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((units + 255) / 256, (int64_t)sm_count() * 16));
-      return launch("expand_edges", s, [&] {
-        if (vec)
-          k_expand<true><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out,
-                                              sort_hist_area(bb.scratch), bb.derr);
+      unsigned long long* hist = sort_hist_area(bb.scratch);
+      return launch(write ? "expand_edges" : "edge_histograms", s, [&] {
+        if (vec && write)
+          k_expand<true, true><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out, hist,
+                                                    bb.derr);
+        else if (vec)
+          k_expand<true, false><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out, hist,
+                                                     bb.derr);
+        else if (write)
+          k_expand<false, true><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out, hist,
+                                                     bb.derr);
         else
-          k_expand<false><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out,
-                                               sort_hist_area(bb.scratch), bb.derr);
+          k_expand<false, false><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out, hist,
+                                                      bb.derr);
       });
+    };
+    // sort of `len` edges from s_in/d_in into keys_a/keys_b at e0
+    auto expand_sort = [&](const int32_t* s_in, const int32_t* d_in, int64_t e0, int64_t len, uint64_t** out) {
+      wedge_status est = sort_clear_hist(bb.scratch, s);
+      const bool fuse = len >= 2;
+      if (est == WEDGE_OK) est = expand(s_in, d_in, e0, len, !fuse);
+      if (est != WEDGE_OK) return est;
+      const SortEdges edges{s_in, d_in, n_vertices, b, sentinel};
+      return radix_sort_u64(bb.keys_a + e0, bb.keys_b + e0, len, 2 * (int)b, bb.scratch, bb.derr, s, out, true, 0,
+                            nullptr, true, fuse ? &edges : nullptr);
     };
     uint64_t* sorted = nullptr;
     if (device_accessible(src) && device_accessible(dst)) {
-      if ((st = sort_clear_hist(bb.scratch, s)) != WEDGE_OK) return bail(st);
-      if ((st = expand(src, dst, 0, n_edges)) != WEDGE_OK) return bail(st);
-      st = radix_sort_u64(bb.keys_a, bb.keys_b, n_edges, 2 * (int)b, bb.scratch, bb.derr, s, &sorted, true);
-      if (st != WEDGE_OK) return bail(st);
+      if ((st = expand_sort(src, dst, 0, n_edges, &sorted)) != WEDGE_OK) return bail(st);
     } else {
       // Host edge list: it lands group by group in the adjacency buffer
       // (2 n_edges int32, unused until the rows are placed: sources, then
@@ -503,11 +512,8 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
       const int64_t group = host_group_edges(n_edges);
       uint64_t* runs = (passes & 1) ? bb.keys_b : bb.keys_a;
       auto group_work = [&](int64_t e0, int64_t len) {
-        wedge_status gst = sort_clear_hist(bb.scratch, s);
-        if (gst == WEDGE_OK) gst = expand(g->adj + e0, g->adj + n_edges + e0, e0, len);
         uint64_t* gs = nullptr;
-        if (gst == WEDGE_OK)
-          gst = radix_sort_u64(bb.keys_a + e0, bb.keys_b + e0, len, 2 * (int)b, bb.scratch, bb.derr, s, &gs, true);
+        wedge_status gst = expand_sort(g->adj + e0, g->adj + n_edges + e0, e0, len, &gs);
         if (gst == WEDGE_OK && gs != runs + e0) {  // a one-key group is not moved by the sort
           const cudaError_t ce = cudaMemcpyAsync(runs + e0, gs, (size_t)len * sizeof(uint64_t),
                                                  cudaMemcpyDeviceToDevice, s);

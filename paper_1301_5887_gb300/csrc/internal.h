@@ -48,12 +48,30 @@ struct SortEmit {
   int32_t* count;
 };
 
+// Keys of the first pass computed from an edge list instead of read (CSR
+// build): key j = edge_key(src[j], dst[j]) (device.cuh); the sort's keys
+// array is then not read.
+struct SortEdges {
+  const int32_t* src;
+  const int32_t* dst;
+  int32_t n_vertices;
+  uint32_t b;
+  uint64_t sentinel;
+};
+
 // Stable LSD sort of the key bits [shift0, shift0 + bits); shift0 a multiple
 // of 8. With emit (shift0 >= 32) the last pass places instead of writing keys
 // and *sorted is not meaningful; n must be at least 2.
+// first_pass_unstable: every nonzero bit of every key lies in the sorted range
+// (keys equal in it are identical) and the lowest digit is evenly spread, so
+// the first pass may rank by one shared atomic per key without stability.
+// edges (shift0 = 0, first_pass_unstable, hist_ready): the first pass computes
+// the keys from the edge list; keys is not read (it is written by later
+// passes, as without edges).
 wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, void* scratch, uint32_t* derr,
                             cudaStream_t s, uint64_t** sorted, bool hist_ready, int shift0 = 0,
-                            const SortEmit* emit = nullptr);
+                            const SortEmit* emit = nullptr, bool first_pass_unstable = false,
+                            const SortEdges* edges = nullptr);
 
 // Merge of sorted runs (merge.cu): keys holds runs of `run` keys each (run a
 // multiple of MERGE_RUN_MULTIPLE; the last run may be shorter), each sorted;

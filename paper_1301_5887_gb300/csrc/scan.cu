@@ -22,7 +22,9 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 __device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
 
-template <typename Tin, typename Tout>
+// CHECK: inputs must be >= 0 (DERR_NEGATIVE otherwise) and every prefix must
+// fit the look-back words' 58-bit value field (DERR_OVERFLOW otherwise).
+template <typename Tin, typename Tout, bool CHECK = false>
 __global__ __launch_bounds__(SCAN_THREADS) void k_scan_excl(const Tin* __restrict__ in, Tout* __restrict__ out,
                                                             int64_t n, uint64_t* status, uint32_t* tile_ctr,
                                                             uint32_t* err, Tout* total, int32_t* maxv) {
@@ -45,6 +47,7 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan_excl(const Tin* __restric
       const Tin x = in[g];
       v = (Tout)x;
       if (maxv) local_max = max(local_max, (int32_t)x);
+      if (CHECK && x < (Tin)0) atomicOr(err, DERR_NEGATIVE);
     }
     s_buf[pad(idx)] = v;
   }
@@ -87,6 +90,7 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan_excl(const Tin* __restric
       st_relaxed(st, lb_pack(1, LB_INC, (uint64_t)(excl + tile_total)));
     }
     s_excl = excl;
+    if (CHECK && (uint64_t)(excl + tile_total) > LB_VALUE_MASK) atomicOr(err, DERR_OVERFLOW);
     if (total && tbase + SCAN_TILE >= n) *total = excl + tile_total;
   }
   __syncthreads();
@@ -172,6 +176,9 @@ void* g_noalloc_addr[kNoallocDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
 // per device (host code cannot use the symbol itself as a device pointer).
+// The address belongs to the device's context: after cudaDeviceReset() the
+// cached address is stale, so the entry point must not be used on a device
+// that has been reset (the header says so).
 cudaError_t noalloc_scratch(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -219,13 +226,16 @@ extern "C" wedge_status wedge_degree_offsets_noalloc(const int32_t* deg, int64_t
   // error word and this call's look-back words.
   WEDGE_CUDA_TRY(cudaMemsetAsync(b, 0, NOALLOC_HEADER + (size_t)tiles * sizeof(uint64_t), s),
                  "wedge_degree_offsets_noalloc");
-  k_scan_excl<int32_t, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(deg, off, n, status, ctr, err, off + n,
-                                                                           nullptr);
+  k_scan_excl<int32_t, int64_t, true><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(deg, off, n, status, ctr, err,
+                                                                                 off + n, nullptr);
   WEDGE_CUDA_TRY(cudaGetLastError(), "wedge_degree_offsets_noalloc: launch");
   uint32_t herr = 0;
   WEDGE_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s),
                  "wedge_degree_offsets_noalloc");
   WEDGE_CUDA_TRY(cudaStreamSynchronize(s), "wedge_degree_offsets_noalloc");
+  if (herr & DERR_NEGATIVE) return fail(WEDGE_EINVAL, "wedge_degree_offsets_noalloc: a degree is negative");
+  if (herr & DERR_OVERFLOW)
+    return fail(WEDGE_EOVERFLOW, "wedge_degree_offsets_noalloc: the degree total reaches 2^58");
   if (herr & DERR_TIMEOUT) return fail(WEDGE_ETIMEOUT, "wedge_degree_offsets_noalloc: a look-back wait gave up");
   return WEDGE_OK;
 }

@@ -7,11 +7,17 @@
 // per warp and publishes them for decoupled look-back before ranking, ranks
 // the keys stably with a warp-level multisplit (peer masks from digit-bit
 // ballots) straight into shared memory in digit order, and writes runs of
-// equal digits contiguously.
+// equal digits contiguously. Each CTA also asks the L2 to prefetch the tile
+// that will be claimed one wave of CTAs later (a bulk prefetch), so a tile's
+// loads mostly hit L2 instead of waiting on HBM.
 //
 // Only `bits` bits from bit `shift0` up are sorted (shift0 a multiple of 8),
 // 8 bits per pass; stable, so the result is sorted by that bit range and keeps
-// the input order among equal values.
+// the input order among equal values. A caller whose keys are whole (every
+// nonzero bit lies in the sorted range, so equal values are identical keys)
+// and whose lowest digit is evenly spread may let the first pass, whose input
+// order carries no meaning, rank without stability (one shared atomic per key,
+// which slows down where many keys of a warp share a digit).
 #include "device.cuh"
 #include "internal.h"
 #include "runtime.h"
@@ -82,23 +88,34 @@ struct PassArgs {
   uint64_t* status;      // tiles * RADIX look-back words
   uint32_t* tile_ctr;
   uint32_t* err;
-  SortEmit emit;         // last pass of a transposed-key sort: place instead of writing keys
+  int64_t prefetch_tiles;  // L2 prefetch distance in tiles (0: none; the input is 16-byte aligned otherwise)
+  SortEmit emit;           // last pass of a transposed-key sort: place instead of writing keys
+  SortEdges edges;         // first pass of a CSR build: keys from the edge list
+  uint32_t edge_prefetch;  // bit 0: src, bit 1: dst 16-byte aligned (L2 prefetch allowed)
 };
 
 struct PassSmem {
-  uint64_t keys[SORT_TILE];             // tile in digit order
-  uint64_t goff[RADIX];                 // global index - local position, per digit
-  uint32_t whist[SORT_WARPS][RADIX];    // per-warp digit counts, then running bases
-  uint32_t dstart[RADIX];               // tile-local start of each digit
+  uint64_t keys[SORT_TILE];           // tile in digit order
+  uint64_t goff[RADIX];               // global index - local position, per digit
+  uint32_t whist[SORT_WARPS][RADIX];  // per-warp digit counts, then running positions
+  uint32_t dstart[RADIX];             // tile-local start of each digit
   uint32_t wsum[SORT_WARPS];
   uint32_t tile;
 };
 constexpr size_t PASS_SMEM = sizeof(PassSmem);
 
+// Digit of a key: byte `sel` of its high (HI) or low 32-bit half (digits are
+// byte-aligned, so one never straddles the halves).
+template <bool HI>
+__device__ __forceinline__ uint32_t digit_of(uint64_t k, uint32_t sel) {
+  return __byte_perm(HI ? (uint32_t)(k >> 32) : (uint32_t)k, 0u, 0x4440u | sel);
+}
+
 // Peer mask of this lane's digit d (0..RADIX, RADIX = no key): the lanes of
 // the warp holding the same value. One ballot per digit bit (plus one for the
 // no-key marker unless every lane holds a key), all issued first; a lane
-// differs from this one where a ballot disagrees with this lane's bit.
+// differs from this one where a ballot disagrees with this lane's bit. The
+// cost does not depend on how the digits are distributed.
 // RB: the digit's significant bits (the rest are zero in every key).
 template <bool FULL, int RB>
 __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
@@ -106,8 +123,8 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
 #pragma unroll
   for (int b = 0; b < RB; ++b) m[b] = __ballot_sync(FULL_MASK, (d >> b) & 1u);
   // This lane's bit b spread over all 32 bits, as bit * 0xffffffff: an integer
-  // multiply runs on the FMA pipe, leaving the ALU pipe (ballots, logic ops,
-  // the pass's bottleneck) one instruction per bit fewer than a negation.
+  // multiply runs on the FMA pipe, leaving the ALU pipe (ballots, logic ops)
+  // one instruction per bit fewer than a negation.
   uint32_t differ = 0;
 #pragma unroll
   for (int b = 0; b < RB; ++b) {
@@ -119,21 +136,14 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
   return ~differ;
 }
 
-// Digit of a key: byte `sel` of its high (HI) or low 32-bit half (digits are
-// byte-aligned, so one never straddles the halves).
-template <bool HI>
-__device__ __forceinline__ uint32_t digit_of(uint64_t k, uint32_t sel) {
-  return __byte_perm(HI ? (uint32_t)(k >> 32) : (uint32_t)k, 0u, 0x4440u | sel);
-}
-
 // Stable warp-level rank of the tile's keys, scattered into shared memory in
 // digit order (FULL: every slot of the tile holds a key). whist[warp][d] holds
 // the tile position of this warp's next key of digit d: every peer reads it,
 // the lowest peer advances it past the group, and each key lands at that
 // position plus the number of its peers in lower lanes.
 template <bool HI, bool FULL, int RB>
-__device__ __forceinline__ void rank_and_place(PassSmem& sm, const uint64_t (&k)[SORT_ITEMS], uint32_t sel,
-                                               int nvalid, int warp, int lane) {
+__device__ __forceinline__ void rank_stable(PassSmem& sm, const uint64_t (&k)[SORT_ITEMS], uint32_t sel, int nvalid,
+                                            int warp, int lane) {
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < SORT_ITEMS; ++i) {
@@ -152,14 +162,28 @@ __device__ __forceinline__ void rank_and_place(PassSmem& sm, const uint64_t (&k)
   }
 }
 
+// Unstable rank: each key takes the next position of its digit in its warp's
+// range by a shared atomic (the order among equal digits is arbitrary).
+template <bool HI>
+__device__ __forceinline__ void rank_unstable(PassSmem& sm, const uint64_t (&k)[SORT_ITEMS], uint32_t sel, int nvalid,
+                                              int warp, int lane) {
+#pragma unroll
+  for (int i = 0; i < SORT_ITEMS; ++i) {
+    const int li = warp * (32 * SORT_ITEMS) + i * 32 + lane;
+    if (li < nvalid) sm.keys[atomicAdd(&sm.whist[warp][digit_of<HI>(k[i], sel)], 1u)] = k[i];
+  }
+}
+
 // One LSD pass over a 6144-key tile (three CTAs per SM; the 256 digit owners
 // are threads 0..255):
-//  1. load 16 keys per thread (coalesced) and count digits per warp;
+//  1. claim a tile, ask L2 to prefetch the tile one wave ahead, load 16 keys
+//     per thread (coalesced) and count digits per warp;
 //  2. publish the tile's digit counts to the look-back words at once, so
 //     later tiles need not wait for this tile's ranking;
-//  3. rank keys stably within each warp (ballot-built peer masks; every
-//     peer reads the warp's position counter for its digit, the lowest peer
-//     advances it) and place them in shared memory in digit order;
+//  3. rank keys stably within each warp (ballot-built peer masks; every peer
+//     reads the warp's position counter for its digit, the lowest peer
+//     advances it), or by one shared atomic per key where STABLE is false,
+//     and place them in shared memory in digit order;
 //  4. look back for the tile's global digit offsets (two predecessors per
 //     round trip);
 //  5. write runs of equal digits to their global positions.
@@ -168,7 +192,8 @@ __device__ __forceinline__ void rank_and_place(PassSmem& sm, const uint64_t (&k)
 // its sorted position j, write u to adj[j + emit.row_start[w]] and add the
 // runs of equal w to emit.count[w]. RB < 8: only the digit's low RB bits can
 // be nonzero in any key (the top digit of keys narrower than the passes).
-template <bool HI, bool EMIT, int RB = RADIX_BITS>
+// EDGES (first pass of a CSR build): key j is edge_key(src[j], dst[j]).
+template <bool HI, bool EMIT, bool STABLE, int RB = RADIX_BITS, bool EDGES = false>
 __global__ __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS) void k_sort_pass(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PassSmem& sm = *reinterpret_cast<PassSmem*>(smem_raw);
@@ -179,13 +204,49 @@ __global__ __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS) void k_sort_pass(Pas
   __syncthreads();
   const int64_t tile = sm.tile;
   const int64_t tbase = tile * SORT_TILE;
+  if (a.prefetch_tiles > 0 && tid == 0) {
+    // a whole tile, in bounds, 16-byte aligned (the input is aligned and a
+    // tile is 48 KB of keys, 24 KB of each endpoint array)
+    const int64_t pbase = tbase + a.prefetch_tiles * SORT_TILE;
+    if (pbase + SORT_TILE <= a.n) {
+      if (!EDGES) {
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.in + pbase),
+                     "r"((uint32_t)(SORT_TILE * sizeof(uint64_t)))
+                     : "memory");
+      } else {
+        if (a.edge_prefetch & 1u)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.edges.src + pbase),
+                       "r"((uint32_t)(SORT_TILE * sizeof(int32_t)))
+                       : "memory");
+        if (a.edge_prefetch & 2u)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.edges.dst + pbase),
+                       "r"((uint32_t)(SORT_TILE * sizeof(int32_t)))
+                       : "memory");
+      }
+    }
+  }
 
   // 1. load (item i of lane l in warp w is tile key w*512 + i*32 + l) and count
   uint64_t k[SORT_ITEMS];
+  if (!EDGES) {
 #pragma unroll
-  for (int i = 0; i < SORT_ITEMS; ++i) {
-    const int64_t idx = tbase + warp * (32 * SORT_ITEMS) + i * 32 + lane;
-    k[i] = idx < a.n ? __ldcs(a.in + idx) : ~0ULL;
+    for (int i = 0; i < SORT_ITEMS; ++i) {
+      const int64_t idx = tbase + warp * (32 * SORT_ITEMS) + i * 32 + lane;
+      k[i] = idx < a.n ? __ldcs(a.in + idx) : ~0ULL;
+    }
+  } else {
+    int32_t u[SORT_ITEMS], v[SORT_ITEMS];
+#pragma unroll
+    for (int i = 0; i < SORT_ITEMS; ++i) {
+      const int64_t idx = tbase + warp * (32 * SORT_ITEMS) + i * 32 + lane;
+      u[i] = idx < a.n ? __ldcs(a.edges.src + idx) : 0;
+      v[i] = idx < a.n ? __ldcs(a.edges.dst + idx) : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < SORT_ITEMS; ++i) {
+      const int64_t idx = tbase + warp * (32 * SORT_ITEMS) + i * 32 + lane;
+      k[i] = idx < a.n ? edge_key(u[i], v[i], a.edges.n_vertices, a.edges.b, a.edges.sentinel, a.err) : ~0ULL;
+    }
   }
   const int64_t left = a.n - tbase;
   const int nvalid = left < SORT_TILE ? (int)left : SORT_TILE;
@@ -230,9 +291,10 @@ __global__ __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS) void k_sort_pass(Pas
   }
   __syncthreads();
 
-  // 3. stable warp-level rank, scattered into shared memory in digit order
-  if (nvalid == SORT_TILE) rank_and_place<HI, true, RB>(sm, k, sel, nvalid, warp, lane);
-  else rank_and_place<HI, false, RB>(sm, k, sel, nvalid, warp, lane);
+  // 3. rank into shared memory in digit order
+  if (!STABLE) rank_unstable<HI>(sm, k, sel, nvalid, warp, lane);
+  else if (nvalid == SORT_TILE) rank_stable<HI, true, RB>(sm, k, sel, nvalid, warp, lane);
+  else rank_stable<HI, false, RB>(sm, k, sel, nvalid, warp, lane);
 
   // 4. look-back for the global offset of each digit
   __syncthreads();
@@ -307,8 +369,11 @@ wedge_status sort_clear_hist(void* scratch, cudaStream_t s) {
 }
 
 wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, void* scratch, uint32_t* derr,
-                            cudaStream_t s, uint64_t** sorted, bool hist_ready, int shift0, const SortEmit* emit) {
+                            cudaStream_t s, uint64_t** sorted, bool hist_ready, int shift0, const SortEmit* emit,
+                            bool first_pass_unstable, const SortEdges* edges) {
   *sorted = keys;
+  if (edges && (n < 2 || shift0 != 0 || !first_pass_unstable || !hist_ready || emit))
+    return fail(WEDGE_EINVAL, "radix sort: keys from edges need n >= 2 and a whole-key sort from bit 0");
   if (n <= 1) return WEDGE_OK;
   const int passes = passes_for(bits);
   if (passes < 1 || passes > MAX_PASSES || shift0 < 0 || (shift0 & 7) || shift0 + 8 * passes > 64)
@@ -339,21 +404,21 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
 
   static bool attr_set = false;
   if (!attr_set) {
-    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)PASS_SMEM),
-                   "radix sort: shared memory");
-    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)PASS_SMEM),
-                   "radix sort: shared memory");
-    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)PASS_SMEM),
-                   "radix sort: shared memory");
-    WEDGE_CUDA_TRY(cudaFuncSetAttribute(k_sort_pass<true, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)PASS_SMEM),
-                   "radix sort: shared memory");
+    const void* fns[] = {reinterpret_cast<const void*>(k_sort_pass<false, false, true>),
+                         reinterpret_cast<const void*>(k_sort_pass<true, false, true>),
+                         reinterpret_cast<const void*>(k_sort_pass<false, false, false>),
+                         reinterpret_cast<const void*>(k_sort_pass<true, true, true>),
+                         reinterpret_cast<const void*>(k_sort_pass<true, true, true, 4>),
+                         reinterpret_cast<const void*>(k_sort_pass<false, false, false, RADIX_BITS, true>)};
+    for (const void* f : fns)
+      WEDGE_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PASS_SMEM),
+                     "radix sort: shared memory");
     attr_set = true;
   }
   if (emit && shift0 < 32) return fail(WEDGE_EINVAL, "radix sort: placement needs keys sorted from bit 32");
+  // L2 prefetch one SM count of tiles ahead (tiles are claimed in order, so
+  // that tile is claimed about one wave of CTAs later)
+  const int64_t prefetch = sm_count();
   uint64_t* src = keys;
   uint64_t* dst = alt;
   for (int p = 0; p < passes; ++p) {
@@ -367,16 +432,30 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
     a.status = status;
     a.tile_ctr = ctr + p;
     a.err = derr;
+    a.prefetch_tiles = (reinterpret_cast<uintptr_t>(src) & 15) == 0 ? prefetch : 0;
     a.emit = emit ? *emit : SortEmit{};
+    a.edges = edges ? *edges : SortEdges{};
+    const bool from_edges = edges && p == 0;
+    a.edge_prefetch = 0;
+    if (from_edges) {
+      a.prefetch_tiles = prefetch;
+      a.edge_prefetch = ((reinterpret_cast<uintptr_t>(edges->src) & 15) == 0 ? 1u : 0u) |
+                        ((reinterpret_cast<uintptr_t>(edges->dst) & 15) == 0 ? 2u : 0u);
+    }
     const bool place = emit && p == passes - 1;
+    // the first pass of a whole-key sort may ignore the (meaningless) input order
+    const bool unstable = first_pass_unstable && p == 0 && a.shift < 32 && !place;
     // the placing pass's digit is the top of w: with at most 4 of its bits
     // in use (b = 28: bits 24..27), the rank looks at those 4 alone
     const bool narrow = bits - RADIX_BITS * (passes - 1) <= 4;
     st = launch("sort_onesweep_pass", s, [&] {
-      if (place && narrow) k_sort_pass<true, true, 4><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
-      else if (place) k_sort_pass<true, true><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
-      else if (a.shift >= 32) k_sort_pass<true, false><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
-      else k_sort_pass<false, false><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
+      if (from_edges)
+        k_sort_pass<false, false, false, RADIX_BITS, true><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
+      else if (place && narrow) k_sort_pass<true, true, true, 4><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
+      else if (place) k_sort_pass<true, true, true><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
+      else if (unstable) k_sort_pass<false, false, false><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
+      else if (a.shift >= 32) k_sort_pass<true, false, true><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
+      else k_sort_pass<false, false, true><<<(unsigned)tiles, SORT_THREADS, PASS_SMEM, s>>>(a);
     });
     if (st != WEDGE_OK) return st;
     uint64_t* t = src;

@@ -134,3 +134,15 @@ def test_no_oracle_import_in_product():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "oracle.c" not in text and "liboracle" not in text, f
+
+
+def test_noalloc_binding_checks_its_arguments(lib):
+    """The allocation-free entry point's binding refuses host tensors, wrong
+    dtypes, non-contiguous outputs and short outputs before any device call."""
+    torch = pytest.importorskip("torch")
+    deg = torch.zeros(8, dtype=torch.int32)
+    off = torch.zeros(9, dtype=torch.int64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        wedge.degree_offsets_noalloc(deg, off)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        wedge.degree_offsets_noalloc(deg.numpy(), off.numpy())

@@ -368,7 +368,7 @@ def test_host_input_streams_in_chunks():
     wedge.profile_enable(False)
     wedge.graph_build(hs, hd, n)
     prof = wedge.profile_read()
-    assert prof["expand_edges"]["launches"] == 5
+    assert prof["edge_histograms"]["launches"] == 5  # one per group; the first sort pass reads the edges
     assert prof["merge_runs"]["launches"] == 3  # 5 runs -> 3 -> 2 -> 1
 
 
@@ -399,13 +399,14 @@ def test_profile_counts_launches():
     wedge.sample(g, b, seed=1, k_per_bin=100, k_global=100)
     st = wedge.profile_read()
     wedge.profile_enable(False)
-    for name in ["expand_edges", "sort_onesweep_pass", "dedup_rows", "scan_degrees", "bin_count",
+    for name in ["edge_histograms", "sort_onesweep_pass", "dedup_rows", "scan_degrees", "bin_count",
                  "bin_scatter", "sample_closure"]:
         assert st[name]["launches"] >= 1, name
         assert st[name]["total_ms"] > 0.0, name
     # forward keys over 2 x 10 id bits, transposed keys over the larger endpoint's 10 bits
     assert st["sort_onesweep_pass"]["launches"] == math.ceil(2 * 10 / 8) + math.ceil(10 / 8)
-    assert "sort_histogram" not in st  # digit histograms are accumulated by expand_edges
+    assert "sort_histogram" not in st  # digit histograms come from one pass over the edges
+    assert "expand_edges" not in st  # the first sort pass computes the keys from the edges
 
 
 # ---------------------------------------------------------------------------

@@ -67,3 +67,24 @@ def test_noalloc_rejects_sizes_beyond_maximum():
                                           torch.cuda.current_stream().cuda_stream)
     assert st == 1  # WEDGE_EINVAL, before any device work
     assert b"exceeds the maximum" in lib.wedge_last_error()
+
+
+def test_noalloc_rejects_negative_degrees_and_overflow():
+    lib = wedge.load()
+    deg = torch.zeros(9000, dtype=torch.int32, device="cuda")
+    deg[5000] = -3
+    off = torch.zeros(9001, dtype=torch.int64, device="cuda")
+    with pytest.raises(wedge.WedgeError):
+        wedge.degree_offsets_noalloc(deg, off)
+    assert b"negative" in lib.wedge_last_error()
+    # 2^28 vertices of degree 2^31 - 1: the total (about 2^59) crosses 2^58
+    n = 1 << 28
+    big = torch.full((n,), 2**31 - 1, dtype=torch.int32, device="cuda")
+    offb = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    with pytest.raises(wedge.WedgeError):
+        wedge.degree_offsets_noalloc(big, offb)
+    assert b"2^58" in lib.wedge_last_error()
+    # the next call works again
+    deg[5000] = 3
+    wedge.degree_offsets_noalloc(deg, off)
+    assert int(off[-1].item()) == 3
