@@ -96,6 +96,17 @@ __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src,
     if (sh[i]) atomicAdd(&hist[i], (unsigned long long)sh[i]);
 }
 
+// Ask L2 to prefetch dedup tile `t` of the sorted keys (a whole tile, in
+// bounds; keys 16-byte aligned and a tile is 48 KB). Tiles are taken in order,
+// so a tile one wave of CTAs ahead is read soon after.
+__device__ __forceinline__ void prefetch_tile_l2(const uint64_t* keys, int64_t nkeys, int64_t t) {
+  const int64_t base = t * DEDUP_TILE;
+  if (base + DEDUP_TILE <= nkeys)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(keys + base),
+                 "r"((uint32_t)(DEDUP_TILE * sizeof(uint64_t)))
+                 : "memory");
+}
+
 // A warp's DEDUP_ITEMS x 32 sorted forward keys from wbase (item i of lane l
 // is key wbase + 32 i + l; past the end, the sentinel), and per item the
 // ballot of the lanes holding the first key of a run of equal keys: the
@@ -135,7 +146,7 @@ __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_dedup(const uint64_t* __re
                                                          int tpasses, unsigned long long* __restrict__ thist,
                                                          int32_t* __restrict__ fdeg, uint64_t* __restrict__ tile_excl,
                                                          uint64_t* status, uint32_t* tile_ctr, uint32_t* err,
-                                                         int64_t* n_unique) {
+                                                         int64_t* n_unique, int64_t prefetch_tiles) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_wcount[DEDUP_THREADS / 32];
   __shared__ uint64_t s_excl;
@@ -147,6 +158,7 @@ __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_dedup(const uint64_t* __re
   const int64_t tile = s_tile;
   const int64_t wbase = tile * DEDUP_TILE + warp * (32 * DEDUP_ITEMS);
   const uint64_t vmask = (1ULL << b) - 1ULL;
+  if (prefetch_tiles > 0 && tid == 0) prefetch_tile_l2(keys, nkeys, tile + prefetch_tiles);
 
   uint64_t k[DEDUP_ITEMS];
   uint32_t bal[DEDUP_ITEMS];
@@ -258,10 +270,11 @@ __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_place_fwd(const uint64_t* 
                                                              uint32_t b, uint64_t sentinel,
                                                              const uint64_t* __restrict__ tile_excl,
                                                              const int64_t* __restrict__ boff,
-                                                             int32_t* __restrict__ adj) {
+                                                             int32_t* __restrict__ adj, int64_t prefetch_tiles) {
   __shared__ uint32_t s_wcount[DEDUP_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t tile = blockIdx.x;
+  if (prefetch_tiles > 0 && tid == 0) prefetch_tile_l2(keys, nkeys, tile + prefetch_tiles);
   const int64_t wbase = tile * DEDUP_TILE + warp * (32 * DEDUP_ITEMS);
   const uint64_t vmask = (1ULL << b) - 1ULL;
   uint64_t k[DEDUP_ITEMS];
@@ -537,10 +550,12 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     BUILD_TRY(cudaMemsetAsync(tail, 0, 256 + (size_t)tiles * sizeof(uint64_t), s), "wedge_graph_build");
     uint32_t* ctr = reinterpret_cast<uint32_t*>(tail);
     uint64_t* status = reinterpret_cast<uint64_t*>(tail + 256);
+    // L2 prefetch one SM count of tiles ahead, where the sorted keys are aligned
+    const int64_t key_prefetch = (reinterpret_cast<uintptr_t>(sorted) & 15) == 0 ? sm_count() : 0;
     st = launch("dedup_rows", s, [&] {
       k_dedup<<<(unsigned)tiles, DEDUP_THREADS, 0, s>>>(sorted, n_edges, b, n_vertices, sentinel, tkeys, tpasses,
                                                         sort_hist_area(bb.scratch), bb.fdeg, bb.tile_excl, status,
-                                                        ctr, bb.derr, bb.scalars);
+                                                        ctr, bb.derr, bb.scalars, key_prefetch);
     });
     if (st != WEDGE_OK) return bail(st);
     int64_t m_unique = 0;
@@ -579,7 +594,7 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     if (m_unique > 0) {
       st = launch("place_rows", s, [&] {
         k_place_fwd<<<(unsigned)tiles, DEDUP_THREADS, 0, s>>>(sorted, n_edges, b, sentinel, bb.tile_excl, boff,
-                                                              g->adj);
+                                                              g->adj, key_prefetch);
       });
       if (st != WEDGE_OK) return bail(st);
     }
