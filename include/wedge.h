@@ -565,6 +565,31 @@ WEDGE_API wedge_status wedge_probe_random_read(uint64_t buffer_bytes, uint64_t r
 /* Release cached device memory of the library's pool on the current device. */
 WEDGE_API wedge_status wedge_trim(void);
 
+/* --------------------------------------------------------------------------
+ * Failure-path hooks for tests (no counterpart in the paper). They make a
+ * failure happen on the host or in a bounded device wait, never by a device
+ * fault, so the failure paths of the other entry points can be exercised.
+ * ------------------------------------------------------------------------ */
+/* Bytes of the library's device memory pool on the current device currently
+ * handed out (cudaMemPoolAttrUsedMemCurrent; 0 before the first allocation).
+ * Stream-ordered frees count once the device has reached them. */
+WEDGE_API uint64_t wedge_pool_used_bytes(void);
+/* After `after` more successful device allocations by the library, refuse
+ * the next one: the entry point that asked for it returns WEDGE_ENOMEM as if
+ * the pool were exhausted, and the hook disarms itself. A negative value
+ * disarms it. Process-wide, all threads and devices. */
+WEDGE_API void wedge_test_fail_allocation(int64_t after);
+/* Runs the single-pass scan kernel of step a4 on two tiles of zeros with its
+ * tile ticket starting at 1: the one CTA takes tile 1 and its decoupled
+ * look-back waits for tile 0, whose status word nothing ever sets, with the
+ * wait's poll limit lowered from about a second to spin_limit polls (1 ..
+ * 2^20). The wait gives up, records the timeout in the device error word,
+ * still publishes its prefix and returns, so the call returns WEDGE_ETIMEOUT
+ * and the context stays usable. Allocates and frees its own buffers;
+ * synchronises s. Errors: EINVAL (spin_limit out of range), ENOMEM, ECUDA;
+ * WEDGE_OK only if the wait unexpectedly did not time out. */
+WEDGE_API wedge_status wedge_test_lookback_timeout(uint32_t spin_limit, wedge_stream s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -168,7 +168,7 @@ EXPORTS = ["wedge_status_str", "wedge_last_error", "wedge_version", "wedge_abi_s
            "wedge_batch_free", "wedge_batch_info", "wedge_sample_batch", "wedge_autotune", "wedge_server_create",
            "wedge_server_destroy", "wedge_server_add_graph", "wedge_server_remove_graph", "wedge_server_submit",
            "wedge_server_wait", "wedge_server_stats", "wedge_probe_random_read", "wedge_triangle_stats",
-           "wedge_exact"]
+           "wedge_exact", "wedge_pool_used_bytes", "wedge_test_fail_allocation", "wedge_test_lookback_timeout"]
 
 _lib = None
 
@@ -227,6 +227,9 @@ def load():
         "wedge_probe_random_read": ([u64, u64, P, P], st),
         "wedge_triangle_stats": ([P, P, u64, u64, P, P, P], st),
         "wedge_exact": ([P, P, P, P, P], st),
+        "wedge_pool_used_bytes": ([], u64),
+        "wedge_test_fail_allocation": ([i64], None),
+        "wedge_test_lookback_timeout": ([u32, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -508,6 +511,23 @@ def degree_offsets_noalloc(deg, off, stream=None):
     if off.numel() < n + 1:
         raise ValueError(f"off holds {off.numel()} entries; n + 1 = {n + 1} are needed")
     _check(lib.wedge_degree_offsets_noalloc(deg.data_ptr(), n, off.data_ptr(), _stream_handle(stream)))
+
+
+def pool_used_bytes() -> int:
+    """Bytes of the library's device pool currently handed out (current device)."""
+    return int(load().wedge_pool_used_bytes())
+
+
+def fail_next_allocation(after: int):
+    """Test hook: refuse the library's device allocation that follows `after`
+    more successful ones (WEDGE_ENOMEM); negative disarms."""
+    load().wedge_test_fail_allocation(int(after))
+
+
+def force_lookback_timeout(spin_limit: int, stream=None):
+    """Test hook: a scan whose look-back waits on a status word nothing sets,
+    with the poll limit lowered to spin_limit; raises WedgeError(ETIMEOUT)."""
+    _check(load().wedge_test_lookback_timeout(int(spin_limit), _stream_handle(stream)))
 
 
 def hoeffding_k(eps: float, delta: float) -> int:

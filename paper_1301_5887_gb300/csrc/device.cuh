@@ -42,10 +42,11 @@ __device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
 
 // Exclusive prefix of `tile` for one lane of look-back: walks predecessors
 // until an inclusive prefix is found, summing aggregates on the way.
-// Bounded: after SPIN_LIMIT polls of one word it records DERR_TIMEOUT and
-// returns what it has; the caller still publishes so no one waits forever.
+// Bounded: after spin_limit polls of one word (SPIN_LIMIT unless a test
+// lowers it) it records DERR_TIMEOUT and returns what it has; the caller
+// still publishes so no one waits forever.
 __device__ __forceinline__ uint64_t lookback(const uint64_t* status, int64_t tile, int64_t stride, uint32_t epoch,
-                                             uint32_t* err) {
+                                             uint32_t* err, uint32_t spin_limit = SPIN_LIMIT) {
   uint64_t excl = 0;
   int64_t j = tile - 1;
   while (j >= 0) {
@@ -53,7 +54,7 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t* status, int64_t til
     uint64_t w = ld_relaxed(p);
     uint32_t spins = 0;
     while ((uint32_t)(w >> 60) != epoch || ((w >> 58) & 3ULL) == 0ULL) {
-      if (++spins >= SPIN_LIMIT) {
+      if (++spins >= spin_limit) {
         atomicOr(err, DERR_TIMEOUT);
         return excl;
       }

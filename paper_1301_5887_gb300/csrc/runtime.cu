@@ -3,6 +3,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -18,6 +19,19 @@ thread_local char g_err[512] = "";
 constexpr int kMaxDevices = 64;
 std::mutex g_pool_mu;
 cudaMemPool_t g_pool[kMaxDevices] = {};
+
+// Test hook (wedge_test_fail_allocation): allocations that still succeed
+// before one is refused; negative when disarmed.
+std::atomic<int64_t> g_fail_after{-1};
+
+// True if this allocation is the one the test hook refuses (then disarmed).
+bool refuse_allocation() {
+  int64_t c = g_fail_after.load();
+  while (c >= 0) {
+    if (g_fail_after.compare_exchange_weak(c, c - 1)) return c == 0;
+  }
+  return false;
+}
 
 struct KStat {
   uint64_t launches = 0;
@@ -92,6 +106,8 @@ wedge_status cuda_fail(cudaError_t e, const char* what) {
 wedge_status dalloc(void** p, size_t bytes, cudaStream_t s, const char* what) {
   *p = nullptr;
   if (bytes == 0) bytes = 256;
+  if (refuse_allocation())
+    return fail(WEDGE_ENOMEM, "%s: cannot allocate %zu bytes of device memory (refused by the test hook)", what, bytes);
   cudaError_t err = cudaSuccess;
   cudaMemPool_t pool = pool_for_current(&err);
   if (!pool) return cuda_fail(err, what);
@@ -278,6 +294,28 @@ int wedge_profile_read(wedge_kernel_stat* out, int cap) {
 wedge_status wedge_trim(void) {
   clear_error();
   return trim_pool();
+}
+
+void wedge_test_fail_allocation(int64_t after) { g_fail_after.store(after < 0 ? -1 : after); }
+
+uint64_t wedge_pool_used_bytes(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    pool = g_pool[dev];
+  }
+  if (!pool) return 0;
+  uint64_t used = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return used;
 }
 
 }  // extern "C"

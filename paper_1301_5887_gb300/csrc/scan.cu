@@ -27,7 +27,8 @@ __device__ __forceinline__ int pad(int i) { return i + (i >> 5); }
 template <typename Tin, typename Tout, bool CHECK = false>
 __global__ __launch_bounds__(SCAN_THREADS) void k_scan_excl(const Tin* __restrict__ in, Tout* __restrict__ out,
                                                             int64_t n, uint64_t* status, uint32_t* tile_ctr,
-                                                            uint32_t* err, Tout* total, int32_t* maxv) {
+                                                            uint32_t* err, Tout* total, int32_t* maxv,
+                                                            uint32_t spin_limit = SPIN_LIMIT) {
   __shared__ Tout s_buf[SCAN_TILE + SCAN_TILE / 32];
   __shared__ Tout s_wsum[SCAN_THREADS / 32];
   __shared__ uint32_t s_tile;
@@ -86,7 +87,7 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan_excl(const Tin* __restric
       st_relaxed(st, lb_pack(1, LB_INC, (uint64_t)tile_total));
     } else {
       st_relaxed(st, lb_pack(1, LB_AGG, (uint64_t)tile_total));
-      excl = (Tout)lookback(status, tile, 1, 1, err);
+      excl = (Tout)lookback(status, tile, 1, 1, err, spin_limit);
       st_relaxed(st, lb_pack(1, LB_INC, (uint64_t)(excl + tile_total)));
     }
     s_excl = excl;
@@ -238,4 +239,57 @@ extern "C" wedge_status wedge_degree_offsets_noalloc(const int32_t* deg, int64_t
     return fail(WEDGE_EOVERFLOW, "wedge_degree_offsets_noalloc: the degree total reaches 2^58");
   if (herr & DERR_TIMEOUT) return fail(WEDGE_ETIMEOUT, "wedge_degree_offsets_noalloc: a look-back wait gave up");
   return WEDGE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Test hook: a look-back wait that runs out (wedge_test_lookback_timeout).
+// The scan kernel runs on two tiles of zeros with its ticket counter starting
+// at 1, so the one CTA launched takes tile 1 and waits for tile 0, which no
+// CTA ever takes: a status word that nothing sets. With the spin limit
+// lowered to spin_limit polls, the bounded wait gives up within
+// milliseconds, records DERR_TIMEOUT, publishes and returns.
+// ---------------------------------------------------------------------------
+extern "C" wedge_status wedge_test_lookback_timeout(uint32_t spin_limit, wedge_stream stream) {
+  clear_error();
+  if (spin_limit < 1 || spin_limit > (1u << 20))
+    return fail(WEDGE_EINVAL, "wedge_test_lookback_timeout: spin_limit must be in [1, 2^20]");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t n = 2 * SCAN_TILE;
+  int32_t* in = nullptr;
+  int64_t* out = nullptr;
+  void* scratch = nullptr;
+  uint32_t* derr = nullptr;
+  auto done = [&](wedge_status st) {
+    dfree(in, s);
+    dfree(out, s);
+    dfree(scratch, s);
+    dfree(derr, s);
+    return st;
+  };
+  wedge_status st;
+  if ((st = dalloc_n(&in, (size_t)n, s, "wedge_test_lookback_timeout")) != WEDGE_OK) return done(st);
+  if ((st = dalloc_n(&out, (size_t)n + 1, s, "wedge_test_lookback_timeout")) != WEDGE_OK) return done(st);
+  if ((st = dalloc(&scratch, scan_scratch_bytes(n), s, "wedge_test_lookback_timeout")) != WEDGE_OK) return done(st);
+  if ((st = dalloc_n(&derr, 1, s, "wedge_test_lookback_timeout")) != WEDGE_OK) return done(st);
+  uint32_t* ctr = static_cast<uint32_t*>(scratch);
+  uint64_t* status = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + 256);
+  const uint32_t one = 1;
+  cudaError_t e = cudaMemsetAsync(in, 0, (size_t)n * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, scan_scratch_bytes(n), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctr, &one, sizeof(one), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return done(cuda_fail(e, "wedge_test_lookback_timeout"));
+  st = launch("test_lookback_timeout", s, [&] {
+    k_scan_excl<int32_t, int64_t><<<1, SCAN_THREADS, 0, s>>>(in, out, n, status, ctr, derr, out + n, nullptr,
+                                                             spin_limit);
+  });
+  if (st != WEDGE_OK) return done(st);
+  uint32_t herr = 0;
+  e = cudaMemcpyAsync(&herr, derr, sizeof(herr), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return done(cuda_fail(e, "wedge_test_lookback_timeout"));
+  if (herr & DERR_TIMEOUT)
+    return done(fail(WEDGE_ETIMEOUT, "wedge_test_lookback_timeout: the look-back wait gave up after %u polls",
+                     spin_limit));
+  return done(WEDGE_OK);
 }

@@ -341,6 +341,59 @@ def test_estimates_within_hoeffding_bound(tau, omega):
     assert abs(est["c_hat"] - c) < eps
 
 
+def _cliques_with_pendants(n_cliques, seed):
+    """n_cliques copies of K_8 in which four "heavy" members each carry five
+    pendant leaves (degree 12, bin 4 with tau = 1, omega = 2) and the other
+    four are plain (degree 7, bin 3); vertex ids shuffled."""
+    rng = np.random.default_rng(seed)
+    n = n_cliques * (8 + 4 * 5)
+    perm = rng.permutation(n).astype(np.int32)
+    src, dst = [], []
+    leaf = n_cliques * 8
+    for c in range(n_cliques):
+        members = [8 * c + i for i in range(8)]
+        for a, b in combinations(members, 2):
+            src.append(a)
+            dst.append(b)
+        for h in members[:4]:
+            for _ in range(5):
+                src.append(h)
+                dst.append(leaf)
+                leaf += 1
+    return perm[np.array(src)], perm[np.array(dst)], n
+
+
+def test_class_fractions_per_bin_match_closed_form():
+    """Thm 3.3 / Alg. Phase 4c classes, per bin, by closed form. A plain
+    centre (bin 3) has 21 wedges: both ends plain (3, class 3), one heavy (12,
+    class 2), both heavy (6, class 1), all closed. A heavy centre (bin 4) has
+    66: heavy-heavy 3 (class 3), heavy-plain 12 (class 2), plain-plain 6
+    (class 1), and 45 with a leaf, open (class 0). The exact enumeration and
+    the sampler's class fractions q_c / k_b must both agree; classes 2 and 3
+    differ by far more than the Hoeffding radius, so exchanging them (or any
+    two classes) fails."""
+    src, dst, n = _cliques_with_pendants(60, seed=11)
+    off, adj = oracle.csr(src, dst, n)
+    want = {3: np.array([0, 6, 12, 3]) / 21.0, 4: np.array([45, 6, 12, 3]) / 66.0}
+    ex = oracle.exact(off, adj, 1, 2)
+    centres = {3: 4 * 60, 4: 4 * 60}
+    for b, frac in want.items():
+        assert int(ex["p_b"][b]) == centres[b] * (21 if b == 3 else 66)
+        assert np.array_equal(ex["pbq"][b].astype(np.int64), np.rint(frac * int(ex["p_b"][b])).astype(np.int64))
+    k = 40000
+    r = oracle.sample(off, adj, 1, 2, seed=13, k_per_bin=k, k_global=0)
+    eps = math.sqrt(math.log(2 / 1e-7) / (2 * k))
+    for b, frac in want.items():
+        row = r["counts"][b]
+        assert int(row[0]) == k
+        got = np.array([int(x) for x in row[1:]]) / k
+        assert np.all(np.abs(got - frac) <= eps), (b, got, frac)
+        # the test's power: exchanging classes 2 and 3 moves both fractions by > 2 eps
+        assert abs(frac[2] - frac[3]) > 2 * eps
+    # bins without wedges get no samples
+    assert all(int(r["counts"][b][0]) == 0 for b in range(len(r["counts"])) if b not in want)
+
+
 def test_centre_distribution_chi_square():
     """Centres of the global stream are drawn with probability C(d,2)/p (Sec. 3.2)."""
     from scipy.stats import chisquare
