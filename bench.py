@@ -56,6 +56,9 @@ def parse():
                     help="requests per rate for the serving sweep (the full sweep uses 10000; 0 skips it)")
     ap.add_argument("--serve-rates", default="300,3000", help="arrival rates per second (full sweep: "
                                                              "100,300,1000,3000,5000)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched leg: the configuration the autotuner picks on this mix (thread mapping, 512 "
+                         "threads, 4096-sample tiles) instead of tuning (for profiling the persistent launch)")
     return ap.parse_args()
 
 
@@ -187,6 +190,7 @@ KERNEL_SOURCES = {
     "edge_histograms": ["graph.cu"],
     "probe_random_read": ["probe.cu"],
     "merge_runs": ["merge.cu"],
+    "batch_sample": ["batch.cu", "sample_device.cuh", "device.cuh"],
 }
 
 
@@ -292,8 +296,10 @@ def build_batched_mix(wedge, graphgen, torch, n_graphs=512, seed=3):
     return items, edges
 
 
-def bench_batched(wedge, graphgen, torch):
-    """512 plain wedge_sample calls vs one autotuned persistent launch."""
+def bench_batched(wedge, graphgen, torch, probe_rate=None, probe_spa=None, autotune=True):
+    """512 plain wedge_sample calls vs one autotuned persistent launch; the
+    persistent launch's random-access roofline fraction where DRAM sector
+    counters of that kernel on this mix exist for the current source."""
     import numpy as np
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -302,7 +308,10 @@ def bench_batched(wedge, graphgen, torch):
     setup_s = time.perf_counter() - t0
     reqs = wedge.Requests(items)
     t0 = time.perf_counter()
-    cfg = wedge.autotune(reqs)
+    if autotune:
+        cfg = wedge.autotune(reqs)
+    else:
+        cfg = wedge.LaunchConfig(wedge.MAP_THREAD, wedge.MAP_THREAD, wedge.MAP_THREAD, 512, 4096, 0)
     tune_s = time.perf_counter() - t0
 
     def plain():
@@ -340,6 +349,14 @@ def bench_batched(wedge, graphgen, torch):
     for it in items:
         it["bins"].free()
         it["graph"].free()
+    roof = {"bound": "random-sector", "kernel": "batch_sample", "achieved": None, "peak": None, "frac": None,
+            "dram_sectors_per_sample": None}
+    ent = ncu_figures("batch_sample")
+    if ent and ent.get("samples") == samples and probe_rate and probe_spa:
+        spl = ent["dram_sectors_per_sample"]
+        roof.update(dram_sectors_per_sample=spl, achieved=spl * samples / batch_s * 32 / 1e9,
+                    peak=probe_rate * probe_spa * 32 / 1e9, unit="GB/s")
+        roof["frac"] = roof["achieved"] / roof["peak"]
     return {"workload": "512 graphs: 256 Kronecker (scale log-uniform 8-22) + 256 Chung-Lu (exponent 2.0-2.6, "
                         "mean degree 8-64, 2^10-2^22 vertices); per-bin and global budgets log-uniform 1e3-1e6",
             "graphs": len(items), "generated_edges": edges, "samples": samples,
@@ -347,8 +364,8 @@ def bench_batched(wedge, graphgen, torch):
             "batched_s": batch_s, "batched_gwedges_per_s": samples / batch_s / 1e9,
             "replay_s": replay_s, "replay_gwedges_per_s": samples / replay_s / 1e9,
             "speedup": plain_s / batch_s, "identical_to_plain": bool(identical),
-            "tuned_config": cfg.as_dict(), "tiles": info["tiles"], "persistent_grid": info["grid"],
-            "setup_s": setup_s, "tune_s": tune_s}
+            "tuned_config": cfg.as_dict(), "autotuned": autotune, "tiles": info["tiles"],
+            "persistent_grid": info["grid"], "setup_s": setup_s, "tune_s": tune_s, "roofline": roof}
 
 
 def bench_serving(wedge, graphgen, torch, rates, n_requests, n_graphs=64, seed=5, upload_frac=0.01):
@@ -381,8 +398,12 @@ def bench_serving(wedge, graphgen, torch, rates, n_requests, n_graphs=64, seed=5
         torch.cuda.synchronize()
         return s, d, n
 
+    # Admission: at most ~50 ms of queued work at the GPU's ~10 Gwedges/s;
+    # batches capped at ~6 ms of work; one GPU-filling batch at a time.
     srv = wedge.Server(hbm_budget_bytes=150 * 10**9, slots=2,
-                       launch={"block_threads": 512, "samples_per_tile": 4096, "flags": wedge.BATCH_DIRECT})
+                       launch={"block_threads": 512, "samples_per_tile": 4096, "flags": wedge.BATCH_DIRECT},
+                       max_batch_samples=64_000_000, max_queued_samples=500_000_000,
+                       gpu_filling_samples=2_000_000)
     ids, plain = [], []
     for i in range(n_graphs):
         s, d, n = gen_edges(i)
@@ -422,9 +443,14 @@ def bench_serving(wedge, graphgen, torch, rates, n_requests, n_graphs=64, seed=5
                 th = threading.Thread(target=uploader, args=(j,))
                 th.start()
                 up_threads.append(th)
-            tickets[j] = srv.submit(ids[gi], sd, eps=eps, delta=0.001)
+            try:
+                tickets[j] = srv.submit(ids[gi], sd, eps=eps, delta=0.001)
+            except wedge.WedgeError as e:  # admission control: the queue holds ~50 ms of work
+                if e.status != wedge.EBUSY:
+                    raise
         for t in tickets:
-            srv.wait(t)
+            if t is not None:
+                srv.wait(t)
         for th in up_threads:
             th.join()
         st = srv.stats(reset=True)
@@ -456,7 +482,8 @@ def bench_serving(wedge, graphgen, torch, rates, n_requests, n_graphs=64, seed=5
             return v[max(1, int(np.ceil(p * len(v)))) - 1]
 
         out.append({"rate_per_s": rate, "requests": n_requests,
-                    "served": {"p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+                    "served": {"rejected": int(st["rejected_requests"]),
+                               "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
                                "gwedges_per_s": st["samples"] / st["span_s"] / 1e9 if st["span_s"] else None,
                                "requests_per_s": st["completed"] / st["span_s"] if st["span_s"] else None,
                                "mean_batch_requests": st["mean_batch_requests"], "batches": st["batches"]},
@@ -470,7 +497,11 @@ def bench_serving(wedge, graphgen, torch, rates, n_requests, n_graphs=64, seed=5
         g.free()
     return {"workload": f"{n_graphs} resident graphs (half Kronecker, half Chung-Lu, scales 14-24) under a 150 GB "
                         f"budget; Poisson arrivals; eps in {{0.01, 0.005, 0.002}}, delta 0.001; "
-                        f"{upload_frac:.0%} uploads", "resident_bytes": res_bytes, "rates": out}
+                        f"{upload_frac:.0%} uploads",
+            "policy": "batches in arrival order up to 64M samples; one GPU-filling (>= 2M samples) batch at a time, "
+                      "smaller requests overtake queued large ones; submits refused (WEDGE_EBUSY) past 500M queued "
+                      "samples; latency percentiles over admitted requests",
+            "resident_bytes": res_bytes, "rates": out}
 
 
 def bench_rounding(wedge, graphgen, torch, g, b, iid_sampling_ms, reps=3, var_scale=18, var_seeds=24):
@@ -545,6 +576,32 @@ def bench_sorted_closure(wedge, g, b, reps=3):
             row[name + "_counts"] = c.counts_matrix()
         row["identical"] = bool(np.array_equal(row.pop("inline_counts"), row.pop("sorted_counts")))
         out.append(row)
+    return out
+
+
+def compact_summary(value, ms_step, gwps, roofline, sampling_roofline, e2e, batched, serving):
+    """The headline figures in a few hundred bytes (the end of the JSON line)."""
+    def r(x, nd=4):
+        return round(x, nd) if isinstance(x, float) else x
+    out = {"s_per_Medge": value, "ms_per_step": r(ms_step, 2), "gwedges_checked_per_s": r(gwps, 3),
+           "sort_pass_frac_of_copy_peak": r(roofline["frac"], 3),
+           "sampler_frac_of_random_access_peak": r(sampling_roofline.get("frac"), 3),
+           "e2e_ms_per_step": r(e2e.get("ms_per_step"), 1) if e2e else None,
+           "e2e_h2d_link_gbs": r(e2e.get("h2d_link_gbs"), 1) if e2e else None}
+    if batched:
+        out["batched"] = {"plain_gwps": r(batched["plain_gwedges_per_s"], 3),
+                          "batched_gwps": r(batched["batched_gwedges_per_s"], 3),
+                          "replay_gwps": r(batched["replay_gwedges_per_s"], 3),
+                          "speedup": r(batched["speedup"], 3), "identical_to_plain": batched["identical_to_plain"],
+                          "roofline_frac": r(batched.get("roofline", {}).get("frac"), 3)}
+    if serving:
+        out["serving"] = [{"rate": row["rate_per_s"],
+                           "served_p50_ms": r(row["served"]["p50_ms"], 2), "served_p99_ms": r(row["served"]["p99_ms"], 2),
+                           "plain_p50_ms": r(row["plain"]["p50_ms"], 2), "plain_p99_ms": r(row["plain"]["p99_ms"], 2),
+                           "served_gwps": r(row["served"]["gwedges_per_s"], 3),
+                           "plain_gwps": r(row["plain"]["gwedges_per_s"], 3),
+                           "rejected": row["served"].get("rejected", 0)}
+                          for row in serving["rates"]]
     return out
 
 
@@ -728,9 +785,28 @@ def run_ours(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
         d2h = 8 + 16 + 2 * 8 * info["n_bins"] + 4 + 8 * (4 * info["n_streams"] + 34 * 34)
+        # One more step with the library's per-launch CUDA events on: device
+        # time per kernel, and the rest of the wall time (the main stream
+        # waiting for host copies, host work between calls).
+        wedge.profile_reset()
+        wedge.profile_enable(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(hsrc, hdst)
+        torch.cuda.synchronize()
+        prof_wall = (time.perf_counter() - t0) * 1e3
+        wedge.profile_enable(False)
+        eprof = wedge.profile_read()
+        kernel_ms = sum(v["total_ms"] for v in eprof.values())
         e2e = {"value": dt / (world * m / 1e6), "unit": "s/Medge", "h2d_bytes_per_step": 8 * n_edges,
                "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "step_ms": [x * 1e3 for x in times],
-               "h2d_link_gbs": link_gbs, "counts_identical_to_device_input": same_as_device}
+               "h2d_link_gbs": link_gbs, "h2d_ms_at_link_rate": 8 * n_edges / link_gbs / 1e6,
+               "counts_identical_to_device_input": same_as_device,
+               "breakdown": {"profiled_step_ms": prof_wall, "kernel_ms": kernel_ms,
+                             "not_in_kernels_ms": prof_wall - kernel_ms,
+                             "kernels_ms": {k: round(v["total_ms"], 3) for k, v in
+                                            sorted(eprof.items(), key=lambda kv: -kv[1]["total_ms"])},
+                             "launches": {k: v["launches"] for k, v in eprof.items()}}}
         del hsrc, hdst
 
     # Triangle statistics (Sec. 5.7): k global-stream samples, closed ones
@@ -780,7 +856,8 @@ def run_ours(args):
     if not args.no_batched:
         wedge.trim()
         torch.cuda.empty_cache()
-        batched = bench_batched(wedge, graphgen, torch)
+        batched = bench_batched(wedge, graphgen, torch, probe_rate=probe, probe_spa=spa,
+                                autotune=not args.no_autotune)
         wedge.trim()
 
     cpu = None
@@ -792,6 +869,8 @@ def run_ours(args):
                "seconds": dt, "gwedges_checked_per_s": ns / dt / 1e9}
 
     if rank == 0:
+        # Bulky detail first; the compact figures the step is judged by come
+        # last, so that a reader of the line's tail sees them.
         line = {"metric": METRIC, "value": value, "unit": "s/Medge", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -801,13 +880,17 @@ def run_ours(args):
                            "bins": info["n_bins"], "samples_per_step": info["samples"],
                            "l2": f"inputs {8 * n_edges / 1e9:.1f} GB > 129 MB L2, no flush needed",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "kernels": kernels, "triangle_stats": tri, "rounding": rounding, "sorted_closure": sorted_cl,
+                "batched": batched, "serving": serving,
+                "estimates": {"c_hat": info["c_hat"], "c_hat_global": info["c_hat_global"]},
                 "gwedges_checked_per_s": gwps, "sampling_ms": samp_ms,
                 "s_per_M_generated_edges": {"device": (ms_step / 1e3) / (world * n_edges / 1e6),
                                             "e2e": (e2e["ms_per_step"] / 1e3) / (world * n_edges / 1e6)
-                                            if e2e and e2e.get("ms_per_step") else None}, "batched": batched, "serving": serving,
-                "triangle_stats": tri, "rounding": rounding, "sorted_closure": sorted_cl, "roofline": roofline, "sampling_roofline": sampling_roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
-                "clocks": clk, "kernels": kernels,
-                "estimates": {"c_hat": info["c_hat"], "c_hat_global": info["c_hat_global"]}}
+                                            if e2e and e2e.get("ms_per_step") else None},
+                "sampling_roofline": sampling_roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "gpu_launches": launches // 1, "clocks": clk,
+                "summary": compact_summary(value, ms_step, gwps, roofline, sampling_roofline, e2e, batched,
+                                           serving)}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

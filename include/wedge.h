@@ -49,7 +49,8 @@ typedef enum {
   WEDGE_ENOMEM = 2,    /* device or host allocation failed */
   WEDGE_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
   WEDGE_ETIMEOUT = 4,  /* a bounded device-side wait gave up (no fault, context intact) */
-  WEDGE_EOVERFLOW = 5  /* a count does not fit its type (degree >= 2^31, wedges >= 2^64) */
+  WEDGE_EOVERFLOW = 5, /* a count does not fit its type (degree >= 2^31, wedges >= 2^64) */
+  WEDGE_EBUSY = 6      /* the server's queue is full (admission control); nothing was queued */
 } wedge_status;
 
 /* Largest number of bins (bin ids 0 .. WEDGE_MAX_BINS-1; id 0 is never used). */
@@ -328,11 +329,22 @@ WEDGE_API wedge_status wedge_autotune(const wedge_request* reqs, int n_reqs, wed
  * request) are evicted least-recently-used first; if that is not enough
  * the upload fails with ENOMEM and nothing is evicted that is in use.
  * wedge_server_submit queues a sampling request on a resident graph and
- * returns a ticket at once. A dispatcher thread keeps up to `slots` batches
- * in flight on separate CUDA streams; whenever a slot frees up it launches
- * every queued request (up to max_batch_requests) as one batch, so requests
- * that arrive while others run are admitted as slots free up and overlap
- * with them on the GPU. wedge_server_wait blocks until a ticket's request is
+ * returns a ticket at once, unless admission control refuses it: a request's
+ * size is its number of samples (per-bin budget times the graph's bins with
+ * wedges, plus the global budget, with budgets from eps/delta by Thm 3.1
+ * where not given), and a submit that would make the queued samples exceed
+ * max_queued_samples returns WEDGE_EBUSY with nothing queued, so latency
+ * stays bounded when arrivals outrun the GPU. A dispatcher thread keeps up
+ * to `slots` batches in flight on separate CUDA streams; whenever a slot
+ * frees up it launches queued requests as one batch: in arrival order, up to
+ * max_batch_requests requests and max_batch_samples samples (at least one
+ * request). A batch of at least gpu_filling_samples samples keeps every SM
+ * busy on its own; while one runs, another request that large waits for it
+ * and only smaller requests, taken from anywhere in the queue in arrival
+ * order, fill the free slot, so small requests never queue behind two large
+ * ones sharing the GPU. So requests that arrive while others run are
+ * admitted as slots free up and overlap with them on the GPU.
+ * wedge_server_wait blocks until a ticket's request is
  * done and returns its counts, which equal wedge_sample's for the same
  * parameters (the mix never changes a result), and its timing. Thread-safe;
  * destroy drains the queue and frees the resident graphs. The paper runs one
@@ -348,6 +360,9 @@ typedef struct {
   uint32_t reserved;
   uint64_t omega;              /* (0 = 2) */
   wedge_launch_config launch;  /* launch shape of every batch */
+  uint64_t max_batch_samples;  /* 0 = no cap on a batch's samples */
+  uint64_t max_queued_samples; /* 0 = no admission limit */
+  uint64_t gpu_filling_samples; /* 0 = 2,000,000 */
 } wedge_server_config;
 
 typedef struct {
@@ -386,6 +401,8 @@ typedef struct {
   uint64_t resident_bytes;
   uint64_t evictions;
   uint64_t rejected_uploads;
+  uint64_t rejected_requests;  /* submits refused by admission control (WEDGE_EBUSY) */
+  uint64_t queued_samples;     /* samples of the requests waiting for a slot */
 } wedge_server_metrics;
 
 WEDGE_API wedge_status wedge_server_create(const wedge_server_config* cfg, wedge_server** out);

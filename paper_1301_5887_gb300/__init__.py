@@ -34,7 +34,8 @@ FLAG_ROUNDING = 0x4  # per-bin samples allocated per vertex by probabilistic rou
 FLAG_SORTED_CLOSURE = 0x8  # per-bin closure queries radix-sorted, then checked in order (Alg. Phase 3b join)
 
 STATUS = {0: "WEDGE_OK", 1: "WEDGE_EINVAL", 2: "WEDGE_ENOMEM", 3: "WEDGE_ECUDA", 4: "WEDGE_ETIMEOUT",
-          5: "WEDGE_EOVERFLOW"}
+          5: "WEDGE_EOVERFLOW", 6: "WEDGE_EBUSY"}
+EBUSY = 6
 
 
 class WedgeError(RuntimeError):
@@ -116,7 +117,8 @@ BATCH_DIRECT = 1
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
                 ("max_batch_requests", ctypes.c_uint32), ("tau", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
-                ("omega", ctypes.c_uint64), ("launch", LaunchConfig)]
+                ("omega", ctypes.c_uint64), ("launch", LaunchConfig), ("max_batch_samples", ctypes.c_uint64),
+                ("max_queued_samples", ctypes.c_uint64), ("gpu_filling_samples", ctypes.c_uint64)]
 
 
 class ServerRequest(ctypes.Structure):
@@ -137,7 +139,8 @@ class ServerMetrics(ctypes.Structure):
                 ("resident_graphs", ctypes.c_uint32), ("queued", ctypes.c_uint32),
                 ("inflight_batches", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("resident_bytes", ctypes.c_uint64), ("evictions", ctypes.c_uint64),
-                ("rejected_uploads", ctypes.c_uint64)]
+                ("rejected_uploads", ctypes.c_uint64), ("rejected_requests", ctypes.c_uint64),
+                ("queued_samples", ctypes.c_uint64)]
 
 
 class TriangleBox(ctypes.Structure):
@@ -665,7 +668,8 @@ class Server:
     """Continuous-batching request loop over resident graphs."""
 
     def __init__(self, hbm_budget_bytes: int = 0, slots: int = 2, max_batch_requests: int = 0, tau: int = 1,
-                 omega: int = 2, launch=None):
+                 omega: int = 2, launch=None, max_batch_samples: int = 0, max_queued_samples: int = 0,
+                 gpu_filling_samples: int = 0):
         lib = load()
         c = ServerConfig()
         c.hbm_budget_bytes = int(hbm_budget_bytes)
@@ -673,6 +677,9 @@ class Server:
         c.max_batch_requests = int(max_batch_requests)
         c.tau = int(tau)
         c.omega = int(omega)
+        c.max_batch_samples = int(max_batch_samples)
+        c.max_queued_samples = int(max_queued_samples)
+        c.gpu_filling_samples = int(gpu_filling_samples)
         lc = _config(launch)
         if lc is not None:
             c.launch = lc

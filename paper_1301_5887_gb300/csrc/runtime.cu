@@ -248,6 +248,7 @@ const char* wedge_status_str(wedge_status st) {
     case WEDGE_ECUDA: return "WEDGE_ECUDA";
     case WEDGE_ETIMEOUT: return "WEDGE_ETIMEOUT";
     case WEDGE_EOVERFLOW: return "WEDGE_EOVERFLOW";
+    case WEDGE_EBUSY: return "WEDGE_EBUSY";
   }
   return "WEDGE_UNKNOWN";
 }

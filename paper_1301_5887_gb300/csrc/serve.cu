@@ -5,13 +5,18 @@
 // resident) and admitted against an HBM budget: the resident footprint plus
 // an upload's build scratch must fit, evicting idle graphs least-recently
 // used first. Sampling requests name a resident graph and carry their own
-// seed and eps/delta (or budgets). A dispatcher thread keeps up to
-// `slots` batches in flight, each on its own CUDA stream: whenever a slot is
-// free it takes every queued request (up to max_batch) and launches them as
-// one batched persistent kernel, so requests that arrive while others are on
-// the GPU join the next batch and run concurrently with the batch in
-// flight. Completion is detected by CUDA events; each request's counts are
-// exactly what wedge_sample would return for it alone.
+// seed and eps/delta (or budgets); a request's size is its sample count.
+// Admission control refuses a submit (WEDGE_EBUSY) that would push the
+// queued samples past a limit. A dispatcher thread keeps up to `slots`
+// batches in flight, each on its own CUDA stream: whenever a slot is free it
+// takes queued requests in arrival order, up to a request count and a sample
+// cap, and launches them as one batched persistent kernel, so requests that
+// arrive while others are on the GPU join the next batch and run
+// concurrently with the batch in flight. A batch large enough to fill the
+// GPU on its own is not paired with another such batch: while one runs,
+// large requests wait and small ones overtake them into the free slot.
+// Completion is detected by polling the slot's stream; each request's counts
+// are exactly what wedge_sample would return for it alone.
 #include <string.h>
 
 #include <algorithm>
@@ -51,6 +56,7 @@ struct Job {
   uint64_t ticket;
   wedge_server_request req;
   double t_submit;
+  uint64_t samples;  // the request's size: per-bin budgets over the bins with wedges, plus the global budget
 };
 
 struct Result {
@@ -65,7 +71,23 @@ struct Inflight {
   int slot = -1;
   std::vector<Job> jobs;
   double t_dispatch = 0.0;
+  uint64_t samples = 0;
 };
+
+constexpr uint64_t kDefaultFillingSamples = 2000000;
+
+// Samples a request draws on a graph with these bins (the budgets of
+// wedge_sample: explicit, else Thm 3.1 from eps and delta).
+uint64_t request_samples(const wedge_server_request& r, const wedge_bins* b) {
+  uint64_t total = 0;
+  if (!(r.flags & WEDGE_FLAG_NO_BINS)) {
+    const uint64_t k = r.k_per_bin ? r.k_per_bin : wedge_hoeffding_k(r.eps, r.delta);
+    for (uint32_t i = 0; i < b->info.n_bins; ++i)
+      if (b->info.p_b[i] > 0) total += k;
+  }
+  if (!(r.flags & WEDGE_FLAG_NO_GLOBAL)) total += r.k_global ? r.k_global : wedge_hoeffding_k(r.eps, r.delta);
+  return total;
+}
 
 uint64_t graph_bytes(const wedge_graph* g, const wedge_bins* b) {
   const uint64_t n = (uint64_t)g->n;
@@ -103,9 +125,11 @@ struct wedge_server {
   uint64_t resident_bytes = 0;
   bool stop = false;
   std::thread worker;
+  uint64_t queued_samples = 0;
   // statistics
   std::vector<double> latencies_us;
   uint64_t completed = 0, samples = 0, batches = 0, batched_requests = 0, evictions = 0, rejected = 0;
+  uint64_t rejected_requests = 0;
   double t_first_submit = 0.0, t_last_done = 0.0;
 
   void run();
@@ -160,12 +184,31 @@ bool wedge_server::dispatch_locked() {
       break;
     }
   if (slot < 0 || queue.empty()) return false;
+  // While a batch that fills the GPU by itself is in flight, another one that
+  // large would only halve both batches' speed: large requests wait, smaller
+  // ones (in arrival order) take the free slot.
+  const uint64_t filling = cfg.gpu_filling_samples ? cfg.gpu_filling_samples : kDefaultFillingSamples;
+  bool gpu_full = false;
+  for (const Inflight& g : inflight) gpu_full = gpu_full || g.samples >= filling;
+  std::vector<Job> take;
+  uint64_t total = 0;
+  for (auto q = queue.begin(); q != queue.end() && take.size() < cfg.max_batch_requests;) {
+    if (gpu_full && q->samples >= filling) {
+      ++q;
+      continue;
+    }
+    if (!take.empty() && cfg.max_batch_samples && total + q->samples > cfg.max_batch_samples) break;
+    total += q->samples;
+    queued_samples -= q->samples;
+    take.push_back(*q);
+    q = queue.erase(q);
+  }
+  if (take.empty()) return false;
   Inflight f;
   f.slot = slot;
+  f.samples = total;
   std::vector<wedge_request> reqs;
-  while (!queue.empty() && reqs.size() < cfg.max_batch_requests) {
-    Job job = queue.front();
-    queue.pop_front();
+  for (Job& job : take) {
     auto it = graphs.find(job.req.graph_id);
     if (it == graphs.end()) {
       Result& r = results[job.ticket];
@@ -376,10 +419,19 @@ extern "C" wedge_status wedge_server_submit(wedge_server* sv, const wedge_server
     auto it = sv->graphs.find(req->graph_id);
     if (it == sv->graphs.end())
       return fail(WEDGE_EINVAL, "wedge_server_submit: graph %llu is not resident", (unsigned long long)req->graph_id);
+    const uint64_t samples = request_samples(*req, it->second.b);
+    if (sv->cfg.max_queued_samples && sv->queued_samples + samples > sv->cfg.max_queued_samples) {
+      sv->rejected_requests += 1;
+      return fail(WEDGE_EBUSY, "wedge_server_submit: %llu queued samples + %llu would pass the limit of %llu",
+                  (unsigned long long)sv->queued_samples, (unsigned long long)samples,
+                  (unsigned long long)sv->cfg.max_queued_samples);
+    }
     it->second.pending += 1;
     Job job;
     job.ticket = sv->next_ticket++;
     job.req = *req;
+    job.samples = samples;
+    sv->queued_samples += samples;
     job.t_submit = now_us();
     if (sv->t_first_submit == 0.0) sv->t_first_submit = job.t_submit;
     sv->results[job.ticket] = Result();
@@ -423,6 +475,8 @@ extern "C" wedge_status wedge_server_stats(wedge_server* sv, wedge_server_metric
   out->rejected_uploads = sv->rejected;
   out->queued = (uint32_t)sv->queue.size();
   out->inflight_batches = (uint32_t)sv->inflight.size();
+  out->rejected_requests = sv->rejected_requests;
+  out->queued_samples = sv->queued_samples;
   if (!sv->latencies_us.empty()) {
     std::vector<double> v = sv->latencies_us;
     std::sort(v.begin(), v.end());
@@ -442,7 +496,7 @@ extern "C" wedge_status wedge_server_stats(wedge_server* sv, wedge_server_metric
     out->span_s = (sv->t_last_done - sv->t_first_submit) * 1e-6;
   if (reset) {
     sv->latencies_us.clear();
-    sv->completed = sv->samples = sv->batches = sv->batched_requests = 0;
+    sv->completed = sv->samples = sv->batches = sv->batched_requests = sv->rejected_requests = 0;
     sv->t_first_submit = sv->t_last_done = 0.0;
   }
   return WEDGE_OK;

@@ -134,3 +134,64 @@ def test_many_small_requests_batch_together():
     sizes = [srv.wait(t)[1]["batch_requests"] for t in tickets]
     assert max(sizes) > 1  # requests that arrived during the first batch were admitted together
     srv.close()
+
+
+def _request_samples(b, k_bin, k_glob):
+    """A request's size as the server counts it: the per-bin budget over the
+    bins with wedges, plus the global budget."""
+    bi = b.info()
+    return k_bin * int((np.array(bi.p_b[: bi.n_bins], np.uint64) != 0).sum()) + k_glob
+
+
+def test_admission_control_refuses_when_queue_is_full():
+    s, d, n = _edges(4)
+    g = wedge.graph_build(s, d, n)
+    b = wedge.bin(g, tau=1, omega=2)
+    size = _request_samples(b, 50000, 50000)
+    # the queue may hold three such requests; one more waits in the only slot
+    srv = wedge.Server(slots=1, max_queued_samples=3 * size)
+    gid = srv.add_graph(s, d, n)
+    tickets, refused = [], 0
+    for i in range(40):  # submitted far faster than one slot drains them
+        try:
+            tickets.append((srv.submit(gid, 1000 + i, k_per_bin=50000, k_global=50000), 1000 + i))
+        except wedge.WedgeError as e:
+            assert e.status == wedge.EBUSY
+            refused += 1
+    st = srv.stats()
+    assert refused >= 1 and st["rejected_requests"] == refused
+    assert st["queued_samples"] <= 3 * size
+    for t, seed in tickets:  # what was admitted is exact
+        c, _ = srv.wait(t)
+        ref = wedge.sample(g, b, seed=seed, k_per_bin=50000, k_global=50000)
+        assert np.array_equal(c.counts_matrix(), ref.counts_matrix()) and c.closed_global == ref.closed_global
+    assert srv.stats()["queued_samples"] == 0
+    srv.close()
+    b.free()
+    g.free()
+
+
+def test_batches_respect_the_sample_cap_and_large_requests_do_not_pair():
+    s, d, n = _edges(4)
+    g = wedge.graph_build(s, d, n)
+    b = wedge.bin(g, tau=1, omega=2)
+    small = _request_samples(b, 1000, 1000)
+    large = _request_samples(b, 400000, 400000)
+    srv = wedge.Server(slots=2, max_batch_samples=8 * small, gpu_filling_samples=large)
+    gid = srv.add_graph(s, d, n)
+    big = [srv.submit(gid, 1 + i, k_per_bin=400000, k_global=400000) for i in range(3)]
+    little = [srv.submit(gid, 100 + i, k_per_bin=1000, k_global=1000) for i in range(48)]
+    big_t = [srv.wait(t)[1] for t in big]
+    little_t = [srv.wait(t)[1] for t in little]
+    # no batch holds more than 8 small requests' samples (a large one alone)
+    assert all(tm["batch_requests"] == 1 for tm in big_t)
+    assert all(tm["batch_requests"] <= 8 for tm in little_t)
+    # two large requests never ran at the same time
+    spans = sorted((tm["dispatch_us"], tm["done_us"]) for tm in big_t)
+    for (d0, e0), (d1, e1) in zip(spans, spans[1:]):
+        assert d1 >= e0 - 50.0  # dispatched only after the previous large one finished (poll granularity)
+    # small requests overtook the queued large ones
+    assert min(tm["done_us"] for tm in little_t) < max(tm["done_us"] for tm in big_t)
+    srv.close()
+    b.free()
+    g.free()
