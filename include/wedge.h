@@ -563,9 +563,14 @@ WEDGE_API wedge_status wedge_degree_offsets_noalloc(const int32_t* deg, int64_t 
 typedef struct {
   char name[48];
   uint64_t launches;
-  double total_ms; /* 0 unless timing was enabled */
+  double total_ms;       /* 0 unless timing was enabled */
+  double first_start_ms; /* start of the first timed launch, ms after the timing was enabled (-1: none) */
+  double last_end_ms;    /* end of the last timed launch, on the same clock (-1: none) */
 } wedge_kernel_stat;
 
+/* Timing on: CUDA events around each launch (and each host-to-device copy
+ * of a host edge list, named "h2d_copy"), timed against a reference event
+ * recorded when timing is switched on. */
 WEDGE_API void wedge_profile_enable(int enable_timing);
 WEDGE_API void wedge_profile_reset(void);
 /* Fills up to cap entries; returns the number of kernels recorded. Synchronises pending events. */

@@ -93,7 +93,8 @@ class EstimatesStruct(ctypes.Structure):
 
 
 class KernelStat(ctypes.Structure):
-    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("first_start_ms", ctypes.c_double), ("last_end_ms", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -550,7 +551,9 @@ def profile_read() -> dict:
     n = lib.wedge_profile_read(None, 0)
     arr = (KernelStat * max(n, 1))()
     n = lib.wedge_profile_read(arr, n)
-    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms)}
+    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms),
+                                   "first_start_ms": float(arr[i].first_start_ms),
+                                   "last_end_ms": float(arr[i].last_end_ms)}
             for i in range(n)}
 
 

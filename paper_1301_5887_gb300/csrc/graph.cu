@@ -401,8 +401,11 @@ wedge_status stage_groups(const int32_t* src, const int32_t* dst, int64_t n_edge
   for (int64_t i = 0; i < groups; ++i) {
     const int64_t e0 = i * group;
     const int64_t len = std::min(group, n_edges - e0);
-    e = cudaMemcpyAsync(src_stage + e0, src + e0, (size_t)len * 4, cudaMemcpyDefault, cs);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dst_stage + e0, dst + e0, (size_t)len * 4, cudaMemcpyDefault, cs);
+    wedge_status cst = launch("h2d_copy", cs, [&] {
+      e = cudaMemcpyAsync(src_stage + e0, src + e0, (size_t)len * 4, cudaMemcpyDefault, cs);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dst_stage + e0, dst + e0, (size_t)len * 4, cudaMemcpyDefault, cs);
+    });
+    if (e == cudaSuccess && cst != WEDGE_OK) return finish(cst);
     if (e == cudaSuccess) e = cudaEventRecord(copied[i], cs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, copied[i], 0);
     if (e != cudaSuccess) return finish(cuda_fail(e, "wedge_graph_build: staging"));
@@ -520,10 +523,19 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
       // (2 n_edges int32, unused until the rows are placed: sources, then
       // destinations), and each group is expanded and sorted on its own as
       // soon as it has arrived, so the sorting overlaps the transfer over the
-      // host link; the sorted groups are then merged. Every group takes the
-      // same number of passes, so all of them end in the same buffer.
+      // host link. Every group takes the same number of passes, so all of
+      // them end in the same buffer. The sorted groups are merged pairwise in
+      // a binary tree (level L merges two level-(L-1) runs, ping-ponging
+      // between the key buffers), each merge queued as soon as the group that
+      // completes it has been sorted: most of the tree is merged while later
+      // groups still cross the link, and only the merges that wait for the
+      // last group remain after it.
       const int64_t group = host_group_edges(n_edges);
+      const int64_t n_groups = (n_edges + group - 1) / group;
+      int top = 0;
+      while ((int64_t(1) << top) < n_groups) ++top;
       uint64_t* runs = (passes & 1) ? bb.keys_b : bb.keys_a;
+      uint64_t* bufs[2] = {runs, runs == bb.keys_a ? bb.keys_b : bb.keys_a};
       auto group_work = [&](int64_t e0, int64_t len) {
         uint64_t* gs = nullptr;
         wedge_status gst = expand_sort(g->adj + e0, g->adj + n_edges + e0, e0, len, &gs);
@@ -532,12 +544,23 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
                                                  cudaMemcpyDeviceToDevice, s);
           if (ce != cudaSuccess) gst = cuda_fail(ce, "wedge_graph_build: group");
         }
+        // the merges this group completes: level L's pair j spans groups
+        // [j 2^L, (j + 1) 2^L); an unpaired run (past the last group) is copied
+        const int64_t gi = e0 / group;
+        for (int L = 1; L <= top && gst == WEDGE_OK; ++L) {
+          const int64_t span = int64_t(1) << L;
+          if ((gi + 1) % span != 0 && gi != n_groups - 1) break;
+          const int64_t p0 = gi / span * span * group;
+          const int64_t half = span / 2 * group;
+          const int64_t la = std::min(half, n_edges - p0);
+          const int64_t lb = std::min(half, n_edges - p0 - la);
+          gst = merge_two_runs(bufs[(L - 1) & 1], bufs[L & 1], p0, la, lb, bb.scratch, s);
+        }
         return gst;
       };
       if ((st = stage_groups(src, dst, n_edges, group, g->adj, g->adj + n_edges, s, group_work)) != WEDGE_OK)
         return bail(st);
-      st = merge_sorted_runs(runs, runs == bb.keys_a ? bb.keys_b : bb.keys_a, n_edges, group, bb.scratch, s, &sorted);
-      if (st != WEDGE_OK) return bail(st);
+      sorted = bufs[top & 1];
     }
     uint64_t* tkeys = sorted == bb.keys_a ? bb.keys_b : bb.keys_a;
 

@@ -73,14 +73,14 @@ wedge_status radix_sort_u64(uint64_t* keys, uint64_t* alt, int64_t n, int bits, 
                             const SortEmit* emit = nullptr, bool first_pass_unstable = false,
                             const SortEdges* edges = nullptr);
 
-// Merge of sorted runs (merge.cu): keys holds runs of `run` keys each (run a
-// multiple of MERGE_RUN_MULTIPLE; the last run may be shorter), each sorted;
-// pairwise merge passes ping-pong between keys and alt until one run is
-// left, and *merged points at it. scratch: merge_scratch_bytes(n).
+// Merge of sorted runs (merge.cu).
 constexpr int64_t MERGE_RUN_MULTIPLE = 4096;
 size_t merge_scratch_bytes(int64_t n);
-wedge_status merge_sorted_runs(uint64_t* keys, uint64_t* alt, int64_t n, int64_t run, void* scratch, cudaStream_t s,
-                               uint64_t** merged);
+// One merge: the sorted runs in[p0, p0 + la) and in[p0 + la, p0 + la + lb)
+// into out[p0, p0 + la + lb) (la a multiple of MERGE_RUN_MULTIPLE unless
+// lb = 0, which copies). scratch: merge_scratch_bytes(la + lb).
+wedge_status merge_two_runs(const uint64_t* in, uint64_t* out, int64_t p0, int64_t la, int64_t lb, void* scratch,
+                            cudaStream_t s);
 
 // Exclusive scans with decoupled look-back (scan.cu).
 size_t scan_scratch_bytes(int64_t n);

@@ -1,7 +1,8 @@
 // merge.cu — pairwise merge of sorted runs of 64-bit keys.
 //
 // A host edge list is sorted in groups while it crosses the host link; the
-// sorted groups are merged here into one sorted array. Merge path (Green,
+// sorted groups are merged here, pair by pair in a binary tree, into one
+// sorted array. Merge path (Green,
 // McColl and Bader, "GPU merge path: a GPU merging algorithm", 2012): each
 // 4,096-key output tile finds, by binary search along its diagonal, how many
 // of its keys come from each of the two runs, so tiles merge independently.
@@ -14,7 +15,8 @@ namespace {
 
 // Runs of `run` keys (the last one possibly shorter) are merged two by two
 // into runs of 2 run keys; each CTA writes one 4096-key tile of the output,
-// and run is a multiple of the tile, so no tile straddles two pairs.
+// and run is a multiple of the tile, so no tile straddles two pairs (one
+// launch merges one pair: the input is its two runs).
 // 32 keys per thread: more loads in flight and fewer merge-path searches per
 // key than 16 (256 threads) or 8 (512 threads); measured fastest of the three.
 constexpr int MERGE_THREADS = 128;
@@ -129,28 +131,22 @@ __global__ __launch_bounds__(MERGE_THREADS) void k_merge(const uint64_t* __restr
 
 size_t merge_scratch_bytes(int64_t n) { return (size_t)((n + MERGE_TILE - 1) / MERGE_TILE + 1) * sizeof(int64_t); }
 
-wedge_status merge_sorted_runs(uint64_t* keys, uint64_t* alt, int64_t n, int64_t run, void* scratch, cudaStream_t s,
-                               uint64_t** merged) {
-  *merged = keys;
-  if (run < 1 || run % MERGE_TILE) return fail(WEDGE_EINVAL, "merge: run length %lld", (long long)run);
+wedge_status merge_two_runs(const uint64_t* in, uint64_t* out, int64_t p0, int64_t la, int64_t lb, void* scratch,
+                            cudaStream_t s) {
+  if (la < 1 || lb < 0 || (lb > 0 && la % MERGE_TILE))
+    return fail(WEDGE_EINVAL, "merge: runs of %lld and %lld keys", (long long)la, (long long)lb);
+  const int64_t n = la + lb;
   const int64_t tiles = (n + MERGE_TILE - 1) / MERGE_TILE;
   if (tiles > (int64_t)INT32_MAX) return fail(WEDGE_EINVAL, "merge: too many keys (%lld)", (long long)n);
   int64_t* split = static_cast<int64_t*>(scratch);
-  uint64_t* src = keys;
-  uint64_t* dst = alt;
-  for (; run < n; run *= 2) {
-    wedge_status st = launch("merge_partition", s, [&] {
-      k_merge_partition<<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(src, n, run, tiles, split);
-    });
-    if (st != WEDGE_OK) return st;
-    st = launch("merge_runs", s, [&] { k_merge<<<(unsigned)tiles, MERGE_THREADS, 0, s>>>(src, dst, n, run, tiles, split); });
-    if (st != WEDGE_OK) return st;
-    uint64_t* t = src;
-    src = dst;
-    dst = t;
-  }
-  *merged = src;
-  return WEDGE_OK;
+  // the pair as the whole input: one run of la keys followed by lb keys
+  wedge_status st = launch("merge_partition", s, [&] {
+    k_merge_partition<<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(in + p0, n, la, tiles, split);
+  });
+  if (st != WEDGE_OK) return st;
+  return launch("merge_runs", s, [&] {
+    k_merge<<<(unsigned)tiles, MERGE_THREADS, 0, s>>>(in + p0, out + p0, n, la, tiles, split);
+  });
 }
 
 }  // namespace wedge

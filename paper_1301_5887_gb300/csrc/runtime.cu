@@ -36,6 +36,8 @@ bool refuse_allocation() {
 struct KStat {
   uint64_t launches = 0;
   double total_ms = 0.0;
+  double first_ms = -1.0;  // earliest start after g_ref
+  double last_ms = -1.0;   // latest end after g_ref
 };
 struct Pending {
   std::string name;
@@ -43,6 +45,7 @@ struct Pending {
 };
 std::mutex g_prof_mu;
 bool g_timing = false;
+cudaEvent_t g_ref = nullptr;  // recorded when timing is switched on
 std::map<std::string, KStat> g_stats;
 std::vector<Pending> g_pending;
 std::vector<cudaEvent_t> g_free_events;
@@ -255,7 +258,17 @@ const char* wedge_status_str(wedge_status st) {
 
 void wedge_profile_enable(int enable_timing) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
+  const bool was = g_timing;
   g_timing = enable_timing != 0;
+  if (g_timing && !was) {
+    if (!g_ref && cudaEventCreate(&g_ref) != cudaSuccess) {
+      cudaGetLastError();
+      g_ref = nullptr;
+    }
+    // on the legacy default stream: ordered after work already queued on the
+    // blocking streams, and a clock for the launches that follow
+    if (g_ref && cudaEventRecord(g_ref, 0) != cudaSuccess) cudaGetLastError();
+  }
 }
 
 void wedge_profile_reset(void) {
@@ -273,8 +286,17 @@ int wedge_profile_read(wedge_kernel_stat* out, int cap) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   for (auto& p : g_pending) {
     float ms = 0.f;
-    if (cudaEventSynchronize(p.e1) == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess)
-      g_stats[p.name].total_ms += ms;
+    if (cudaEventSynchronize(p.e1) == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+      KStat& k = g_stats[p.name];
+      k.total_ms += ms;
+      float t0 = 0.f, t1 = 0.f;
+      if (g_ref && cudaEventElapsedTime(&t0, g_ref, p.e0) == cudaSuccess &&
+          cudaEventElapsedTime(&t1, g_ref, p.e1) == cudaSuccess) {
+        if (k.first_ms < 0.0 || t0 < k.first_ms) k.first_ms = t0;
+        if (t1 > k.last_ms) k.last_ms = t1;
+      }
+    }
+    cudaGetLastError();
     g_free_events.push_back(p.e0);
     g_free_events.push_back(p.e1);
   }
@@ -286,6 +308,8 @@ int wedge_profile_read(wedge_kernel_stat* out, int cap) {
       strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
       out[i].launches = kv.second.launches;
       out[i].total_ms = kv.second.total_ms;
+      out[i].first_start_ms = kv.second.first_ms;
+      out[i].last_end_ms = kv.second.last_ms;
     }
     ++i;
   }

@@ -369,7 +369,10 @@ def test_host_input_streams_in_chunks():
     wedge.graph_build(hs, hd, n)
     prof = wedge.profile_read()
     assert prof["edge_histograms"]["launches"] == 5  # one per group; the first sort pass reads the edges
-    assert prof["merge_runs"]["launches"] == 3  # 5 runs -> 3 -> 2 -> 1
+    # 5 sorted groups merged pairwise in a binary tree, each merge queued once
+    # its last group is sorted: 3 merges (one a copy of the unpaired run) at
+    # level 1, 2 at level 2, 1 at level 3
+    assert prof["merge_runs"]["launches"] == 3 + 2 + 1
 
 
 @pytest.mark.parametrize("m,n", [(4097, 700), (8193, 700), (32768, 700), (32769, 700), (40961, 200),
