@@ -188,7 +188,28 @@ def load():
         return _lib
     if not os.path.exists(_SO):
         raise ImportError(f"libwedge.so is not built ({_SO}); run __graft_entry__.build() — there is no CPU fallback")
-    lib = ctypes.CDLL(_SO)
+    _lib = _configure(ctypes.CDLL(_SO))
+    return _lib
+
+
+_lib_debug = None
+
+
+def load_debug():
+    """The bounds-checked build, libwedge_debug.so (same C ABI; index checks
+    at gathered-offset accesses report WEDGE_ECUDA instead of faulting). Its
+    handles must not be mixed with those of libwedge.so."""
+    global _lib_debug
+    if _lib_debug is None:
+        path = os.path.join(os.path.dirname(_SO), "libwedge_debug.so")
+        if not os.path.exists(path):
+            raise ImportError(f"libwedge_debug.so is not built ({path}); run __graft_entry__.build()")
+        _lib_debug = _configure(ctypes.CDLL(path))
+    return _lib_debug
+
+
+def _configure(lib):
+    """Argument and result types of every exported function; ABI struct sizes checked."""
     i32, i64, u32, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
     P = ctypes.c_void_p
     st = ctypes.c_int
@@ -244,7 +265,6 @@ def load():
     for i, S in enumerate(_STRUCTS):
         if sizes[i] != ctypes.sizeof(S):
             raise ImportError(f"ABI mismatch for {S.__name__}: C {sizes[i]} bytes, binding {ctypes.sizeof(S)}")
-    _lib = lib
     return lib
 
 

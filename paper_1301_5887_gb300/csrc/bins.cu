@@ -76,7 +76,8 @@ __global__ __launch_bounds__(BIN_THREADS) void k_bin_scatter(const int32_t* __re
                                                              const uint64_t* __restrict__ lo_g, uint32_t nb,
                                                              uint32_t pow2, int64_t n_tiles,
                                                              const int64_t* __restrict__ pos_base,
-                                                             int32_t* __restrict__ L, uint64_t* __restrict__ wedges) {
+                                                             int32_t* __restrict__ L, uint64_t* __restrict__ wedges,
+                                                             int64_t n2, uint32_t* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* s_lo = reinterpret_cast<uint64_t*>(smem);
   int64_t* s_pos = reinterpret_cast<int64_t*>(s_lo + nb);  // [warp][bin]
@@ -122,8 +123,10 @@ __global__ __launch_bounds__(BIN_THREADS) void k_bin_scatter(const int32_t* __re
     if (b != 0xffffffffu) {
       p0 = s_pos[warp * nb + b];
       const int64_t pos = p0 + __popc(peers & lt);
-      L[pos] = (int32_t)(tbase + vl);
-      wedges[pos] = (uint64_t)d * (uint64_t)(d - 1) / 2ULL;
+      if (in_bounds((uint64_t)pos, (uint64_t)n2, err)) {
+        L[pos] = (int32_t)(tbase + vl);
+        wedges[pos] = (uint64_t)d * (uint64_t)(d - 1) / 2ULL;
+      }
     }
     __syncwarp();
     if (b != 0xffffffffu && (peers & lt) == 0) s_pos[warp * nb + b] = p0 + __popc(peers);
@@ -282,7 +285,7 @@ extern "C" wedge_status wedge_bin(const wedge_graph* g, const wedge_bin_params* 
     BIN_TRY(cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "wedge_bin");
     st = launch("bin_scatter", s, [&] {
       k_bin_scatter<<<(unsigned)n_tiles, BIN_THREADS, smem, s>>>(g->deg, n, b->lo_dev, nb, b->pow2, n_tiles, pos_base,
-                                                                 b->L, wedges);
+                                                                 b->L, wedges, n2, derr);
     });
     if (st != WEDGE_OK) return bail(st);
     // W = exclusive prefix of the wedge counts over L, W[n2] = p
@@ -304,6 +307,7 @@ extern "C" wedge_status wedge_bin(const wedge_graph* g, const wedge_bin_params* 
   }
   BIN_TRY(cudaStreamSynchronize(s), "wedge_bin");
   if (herr & DERR_TIMEOUT) return bail(fail(WEDGE_ETIMEOUT, "wedge_bin: a look-back wait gave up"));
+  if (herr & DERR_BOUNDS) return bail(fail(WEDGE_ECUDA, "wedge_bin: an index outside its buffer (bounds-checked build)"));
   // p_b: the wedge prefix across bin b's stretch of L
   for (uint32_t k = 0; k < nb; ++k) inf.p_b[k] = hs[nb + k + 1] - hs[nb + k];
   inf.p_total = hs[2 * nb];

@@ -13,6 +13,26 @@ constexpr uint32_t DERR_BAD_ID = 1u;     // an input id outside [0, n)
 constexpr uint32_t DERR_TIMEOUT = 2u;    // a look-back wait gave up
 constexpr uint32_t DERR_OVERFLOW = 4u;   // a count overflowed
 constexpr uint32_t DERR_NEGATIVE = 8u;   // a count that must be >= 0 was negative
+constexpr uint32_t DERR_BOUNDS = 16u;    // debug build: an index outside its buffer (the access was skipped)
+
+// Index check of the bounds-checked debug build (compiled with
+// -DWEDGE_DEBUG_BOUNDS): true if i < n; otherwise it records DERR_BOUNDS in
+// the call's error word and returns false, and the caller skips the access
+// (or reads a harmless in-range substitute), so a bad index is reported to
+// the host instead of faulting the GPU. Without the flag it is constant true
+// and costs nothing. err == nullptr: not checked.
+__device__ __forceinline__ bool in_bounds(uint64_t i, uint64_t n, uint32_t* err) {
+#ifdef WEDGE_DEBUG_BOUNDS
+  if (err == nullptr || i < n) return true;
+  atomicOr(err, DERR_BOUNDS);
+  return false;
+#else
+  (void)i;
+  (void)n;
+  (void)err;
+  return true;
+#endif
+}
 
 // A look-back wait polls at most this many times (with nanosleep back-off,
 // about a second) before it records DERR_TIMEOUT and stops waiting.

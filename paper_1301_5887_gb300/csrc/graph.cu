@@ -212,7 +212,8 @@ __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_dedup(const uint64_t* __re
   for (int i = 0; i < DEDUP_ITEMS; ++i) {
     if ((bal[i] >> lane) & 1u) {
       const uint32_t w = (uint32_t)(k[i] & vmask);
-      tkeys[pos + __popc(bal[i] & lt)] = ((uint64_t)w << 32) | (k[i] >> b);
+      const uint64_t at = pos + __popc(bal[i] & lt);
+      if (in_bounds(at, (uint64_t)nkeys, err)) tkeys[at] = ((uint64_t)w << 32) | (k[i] >> b);
     }
     pos += __popc(bal[i]);
   }
@@ -223,7 +224,7 @@ __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_dedup(const uint64_t* __re
 // Backward row lengths: runs of equal w in the sorted transposed keys; the
 // last lane of each run within a warp's 32 keys adds the run to bdeg[w].
 __global__ __launch_bounds__(256) void k_count_back(const uint64_t* __restrict__ tkeys, int64_t m,
-                                                    int32_t* __restrict__ bdeg) {
+                                                    int32_t* __restrict__ bdeg, int32_t n, uint32_t* err) {
   const int lane = threadIdx.x & 31;
   const uint32_t le = lanemask_lt() | (1u << lane);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -234,7 +235,7 @@ __global__ __launch_bounds__(256) void k_count_back(const uint64_t* __restrict__
     const uint32_t w_prev = __shfl_up_sync(FULL_MASK, w, 1);
     const uint32_t w_next = __shfl_down_sync(FULL_MASK, w, 1);
     const uint32_t starts = __ballot_sync(FULL_MASK, lane == 0 || w_prev != w);
-    if (j < m && (lane == 31 || w_next != w)) {
+    if (j < m && (lane == 31 || w_next != w) && in_bounds(w, (uint64_t)n, err)) {
       const int start = 31 - __clz(starts & le);
       atomicAdd(bdeg + w, lane - start + 1);
     }
@@ -270,7 +271,8 @@ __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_place_fwd(const uint64_t* 
                                                              uint32_t b, uint64_t sentinel,
                                                              const uint64_t* __restrict__ tile_excl,
                                                              const int64_t* __restrict__ boff,
-                                                             int32_t* __restrict__ adj, int64_t prefetch_tiles) {
+                                                             int32_t* __restrict__ adj, int64_t prefetch_tiles,
+                                                             int32_t n, int64_t adj_len, uint32_t* err) {
   __shared__ uint32_t s_wcount[DEDUP_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t tile = blockIdx.x;
@@ -289,7 +291,11 @@ __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_place_fwd(const uint64_t* 
   for (int i = 0; i < DEDUP_ITEMS; ++i) {
     if ((bal[i] >> lane) & 1u) {
       const uint64_t at = pos + __popc(bal[i] & lt);
-      adj[at + __ldg(boff + (k[i] >> b) + 1)] = (int32_t)(k[i] & vmask);
+      const uint64_t u = k[i] >> b;
+      if (in_bounds(u, (uint64_t)n, err)) {
+        const uint64_t dst = at + __ldg(boff + u + 1);
+        if (in_bounds(dst, (uint64_t)adj_len, err)) adj[dst] = (int32_t)(k[i] & vmask);
+      }
     }
     pos += __popc(bal[i]);
   }
@@ -298,11 +304,14 @@ __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_place_fwd(const uint64_t* 
 // Backward entry j, key (w << 32) | u, goes to j + foff[w]: row w starts at
 // foff[w] + boff[w] and the backward entries of w are j - boff[w] into it.
 __global__ __launch_bounds__(256) void k_place_back(const uint64_t* __restrict__ tkeys, int64_t m,
-                                                    const int64_t* __restrict__ foff, int32_t* __restrict__ adj) {
+                                                    const int64_t* __restrict__ foff, int32_t* __restrict__ adj,
+                                                    int32_t n, int64_t adj_len, uint32_t* err) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
     const uint64_t key = __ldcs(tkeys + j);
-    adj[j + __ldg(foff + (key >> 32))] = (int32_t)(uint32_t)key;
+    if (!in_bounds(key >> 32, (uint64_t)n, err)) continue;
+    const uint64_t dst = j + __ldg(foff + (key >> 32));
+    if (in_bounds(dst, (uint64_t)adj_len, err)) adj[dst] = (int32_t)(uint32_t)key;
   }
 }
 
@@ -593,14 +602,14 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     if (st != WEDGE_OK) return bail(st);
     if (m_unique >= 2) {
       if ((st = dalloc_n(&bb.keys_c, (size_t)m_unique, s, "wedge_graph_build: keys")) != WEDGE_OK) return bail(st);
-      const SortEmit emit{g->adj, bb.foff, bdeg};
+      const SortEmit emit{g->adj, bb.foff, bdeg, nkeys, n_vertices};
       uint64_t* unused = nullptr;
       st = radix_sort_u64(tkeys, bb.keys_c, m_unique, (int)b, bb.scratch, bb.derr, s, &unused, true, 32, &emit);
       if (st != WEDGE_OK) return bail(st);
     } else if (m_unique == 1) {  // one key is sorted already
       st = launch("place_rows", s, [&] {
-        k_count_back<<<1, 256, 0, s>>>(tkeys, m_unique, bdeg);
-        k_place_back<<<1, 256, 0, s>>>(tkeys, m_unique, bb.foff, g->adj);
+        k_count_back<<<1, 256, 0, s>>>(tkeys, m_unique, bdeg, n_vertices, bb.derr);
+        k_place_back<<<1, 256, 0, s>>>(tkeys, m_unique, bb.foff, g->adj, n_vertices, nkeys, bb.derr);
       });
       if (st != WEDGE_OK) return bail(st);
     }
@@ -617,7 +626,7 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     if (m_unique > 0) {
       st = launch("place_rows", s, [&] {
         k_place_fwd<<<(unsigned)tiles, DEDUP_THREADS, 0, s>>>(sorted, n_edges, b, sentinel, bb.tile_excl, boff,
-                                                              g->adj, key_prefetch);
+                                                              g->adj, key_prefetch, n_vertices, nkeys, bb.derr);
       });
       if (st != WEDGE_OK) return bail(st);
     }
@@ -633,6 +642,8 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
   if (e != cudaSuccess) return bail(cuda_fail(e, "wedge_graph_build"));
   if (herr & DERR_BAD_ID) return bail(fail(WEDGE_EINVAL, "wedge_graph_build: a vertex id is outside [0, %d)", n_vertices));
   if (herr & DERR_TIMEOUT) return bail(fail(WEDGE_ETIMEOUT, "wedge_graph_build: a look-back wait gave up"));
+  if (herr & DERR_BOUNDS) return bail(fail(WEDGE_ECUDA, "wedge_graph_build: an index outside its buffer "
+                                                        "(bounds-checked build)"));
   g->n_adj = 2 * hs[0];
   g->max_degree = (int32_t)(hs[1] & 0xffffffff);
   if (g->max_degree < 0) g->max_degree = 0;

@@ -46,6 +46,8 @@ struct SortEmit {
   int32_t* adj;
   const int64_t* row_start;
   int32_t* count;
+  int64_t adj_len;  // entries of adj (checked by the debug build)
+  int64_t rows;     // entries of row_start and count
 };
 
 // Keys of the first pass computed from an edge list instead of read (CSR

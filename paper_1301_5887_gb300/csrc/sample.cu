@@ -54,6 +54,8 @@ struct SampleArgs {
   unsigned long long* q_out;   // [n_streams][4]
   unsigned long long* stats;   // [WEDGE_STAT_BINS][WEDGE_STAT_BINS]
   wedge_record* records;       // global stream records or nullptr
+  int64_t n, n_adj, n_L;       // sizes for the bounds-checked debug build
+  uint32_t* err;
 };
 
 __global__ __launch_bounds__(SAMPLE_THREADS) void k_sample(SampleArgs a) {
@@ -77,7 +79,7 @@ __global__ __launch_bounds__(SAMPLE_THREADS) void k_sample(SampleArgs a) {
   __syncthreads();
   const StreamDesc desc = s_desc;
   const BinTable bt{s_lo, a.nb, a.pow2};
-  const GraphView gv{a.off, a.adj, a.L, a.W};
+  const GraphView gv{a.off, a.adj, a.L, a.W, a.n, a.n_adj, a.n_L, a.err};
   const bool global = desc.tag != 0;
   const uint64_t first = ((uint64_t)blockIdx.x - desc.tile_begin) * SAMPLE_TILE;
   uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
@@ -241,7 +243,8 @@ static wedge_status sample_streams(const wedge_graph* g, const wedge_bins* b, co
 
   StreamDesc* d_streams = nullptr;
   unsigned long long* d_cnt = nullptr;  // [n_streams][4] then stats
-  const size_t n_cnt = streams.size() * 4 + WEDGE_STAT_BINS * WEDGE_STAT_BINS;
+  // [n_streams][4] tallies, the statistics histogram, then the error word
+  const size_t n_cnt = streams.size() * 4 + WEDGE_STAT_BINS * WEDGE_STAT_BINS + 1;
   wedge_status st;
   if ((st = dalloc_n(&d_streams, streams.size(), s, "wedge_sample")) != WEDGE_OK) return st;
   if ((st = dalloc_n(&d_cnt, n_cnt, s, "wedge_sample")) != WEDGE_OK) {
@@ -274,6 +277,10 @@ static wedge_status sample_streams(const wedge_graph* g, const wedge_bins* b, co
   a.q_out = d_cnt;
   a.stats = d_cnt + streams.size() * 4;
   a.records = static_cast<wedge_record*>(sp->records);
+  a.n = g->n;
+  a.n_adj = g->n_adj;
+  a.n_L = inf.n_wedge_vertices;
+  a.err = reinterpret_cast<uint32_t*>(d_cnt + n_cnt - 1);
   st = launch("sample_closure", s, [&] { k_sample<<<(unsigned)tiles, SAMPLE_THREADS, 0, s>>>(a); });
   if (st != WEDGE_OK) return done(st);
 
@@ -282,6 +289,8 @@ static wedge_status sample_streams(const wedge_graph* g, const wedge_bins* b, co
   if (e != cudaSuccess) return done(cuda_fail(e, "wedge_sample"));
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return done(cuda_fail(e, "wedge_sample"));
+  if ((uint32_t)h[n_cnt - 1] & DERR_BOUNDS)
+    return done(fail(WEDGE_ECUDA, "wedge_sample: an index outside its buffer (bounds-checked build)"));
   for (size_t i = 0; i < streams.size(); ++i) {
     const unsigned long long* c = h.data() + 4 * i;
     if (stream_bin[i] >= 0) {

@@ -13,12 +13,25 @@
 namespace wedge {
 
 // One sampling stream: a bin of one graph (tag 0) or all of its wedges (tag 1).
+// n, n_adj, n_L and err are read only by the bounds-checked debug build
+// (err == nullptr: unchecked).
 struct GraphView {
   const int64_t* off;
   const int32_t* adj;
   const int32_t* L;
   const uint64_t* W;
+  int64_t n = 0;
+  int64_t n_adj = 0;
+  int64_t n_L = 0;
+  uint32_t* err = nullptr;
 };
+
+// Debug-build read of a[i] for i < n; an index outside reads a[0] instead
+// (n >= 1 wherever a gather happens) after recording DERR_BOUNDS.
+template <typename T>
+__device__ __forceinline__ T checked_ldg(const T* a, int64_t i, int64_t n, uint32_t* err) {
+  return __ldg(a + (in_bounds((uint64_t)i, (uint64_t)n, err) ? i : 0));
+}
 
 struct Wedge {
   int32_t v0, v1, v2;
@@ -61,20 +74,20 @@ __device__ __forceinline__ Wedge draw_pair_thread(const GraphView& g, int64_t st
     const int64_t mid = lo + ((hi - lo) >> 1);
     if (__ldg(g.W + mid) <= T) lo = mid; else hi = mid;
   }
-  w.v0 = __ldg(g.L + lo);
-  const int64_t o0 = __ldg(g.off + w.v0);
-  w.d0 = __ldg(g.off + w.v0 + 1) - o0;
+  w.v0 = checked_ldg(g.L, lo, g.n_L, g.err);
+  const int64_t o0 = checked_ldg(g.off, w.v0, g.n + 1, g.err);
+  w.d0 = checked_ldg(g.off, (int64_t)w.v0 + 1, g.n + 1, g.err) - o0;
   const uint64_t dm1 = (uint64_t)(w.d0 - 1);
   const uint64_t u = mulhi64((uint64_t)r.r2 | ((uint64_t)r.r3 << 32), (uint64_t)w.d0 * dm1);
   const uint64_t i = u / dm1;
   const uint64_t jp = u - i * dm1;
   const uint64_t j = jp + (jp >= i ? 1ULL : 0ULL);
-  w.v1 = __ldg(g.adj + o0 + (int64_t)i);
-  w.v2 = __ldg(g.adj + o0 + (int64_t)j);
-  o1 = __ldg(g.off + w.v1);
-  w.d1 = __ldg(g.off + w.v1 + 1) - o1;
-  o2 = __ldg(g.off + w.v2);
-  w.d2 = __ldg(g.off + w.v2 + 1) - o2;
+  w.v1 = checked_ldg(g.adj, o0 + (int64_t)i, g.n_adj, g.err);
+  w.v2 = checked_ldg(g.adj, o0 + (int64_t)j, g.n_adj, g.err);
+  o1 = checked_ldg(g.off, w.v1, g.n + 1, g.err);
+  w.d1 = checked_ldg(g.off, (int64_t)w.v1 + 1, g.n + 1, g.err) - o1;
+  o2 = checked_ldg(g.off, w.v2, g.n + 1, g.err);
+  w.d2 = checked_ldg(g.off, (int64_t)w.v2 + 1, g.n + 1, g.err) - o2;
   w.closed = false;
   return w;
 }
@@ -84,7 +97,10 @@ __device__ __forceinline__ Wedge draw_wedge_thread(const GraphView& g, int64_t s
                                                    uint64_t wbase, const Philox4& r) {
   int64_t o1, o2;
   Wedge w = draw_pair_thread(g, start, len, p, wbase, r, o1, o2);
-  w.closed = closed_wedge(g.adj, w.v1, w.v2, o1, w.d1, o2, w.d2);
+  // the closure search stays inside the two rows, which must lie in adj
+  const bool rows_ok = in_bounds((uint64_t)(o1 + w.d1), (uint64_t)g.n_adj + 1, g.err) &&
+                       in_bounds((uint64_t)(o2 + w.d2), (uint64_t)g.n_adj + 1, g.err);
+  w.closed = rows_ok && closed_wedge(g.adj, w.v1, w.v2, o1, w.d1, o2, w.d2);
   return w;
 }
 

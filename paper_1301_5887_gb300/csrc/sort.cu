@@ -143,7 +143,7 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
 // position plus the number of its peers in lower lanes.
 template <bool HI, bool FULL, int RB>
 __device__ __forceinline__ void rank_stable(PassSmem& sm, const uint64_t (&k)[SORT_ITEMS], uint32_t sel, int nvalid,
-                                            int warp, int lane) {
+                                            int warp, int lane, uint32_t* err) {
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < SORT_ITEMS; ++i) {
@@ -156,7 +156,8 @@ __device__ __forceinline__ void rank_stable(PassSmem& sm, const uint64_t (&k)[SO
     __syncwarp();  // every peer has read the counter before the lowest one moves it
     if (has) {
       if (below == 0) sm.whist[warp][d] = next + __popc(peers);
-      sm.keys[next + __popc(below)] = k[i];
+      const uint32_t pos = next + __popc(below);
+      if (in_bounds(pos, SORT_TILE, err)) sm.keys[pos] = k[i];
     }
     __syncwarp();
   }
@@ -166,11 +167,14 @@ __device__ __forceinline__ void rank_stable(PassSmem& sm, const uint64_t (&k)[SO
 // range by a shared atomic (the order among equal digits is arbitrary).
 template <bool HI>
 __device__ __forceinline__ void rank_unstable(PassSmem& sm, const uint64_t (&k)[SORT_ITEMS], uint32_t sel, int nvalid,
-                                              int warp, int lane) {
+                                              int warp, int lane, uint32_t* err) {
 #pragma unroll
   for (int i = 0; i < SORT_ITEMS; ++i) {
     const int li = warp * (32 * SORT_ITEMS) + i * 32 + lane;
-    if (li < nvalid) sm.keys[atomicAdd(&sm.whist[warp][digit_of<HI>(k[i], sel)], 1u)] = k[i];
+    if (li < nvalid) {
+      const uint32_t pos = atomicAdd(&sm.whist[warp][digit_of<HI>(k[i], sel)], 1u);
+      if (in_bounds(pos, SORT_TILE, err)) sm.keys[pos] = k[i];
+    }
   }
 }
 
@@ -292,9 +296,9 @@ __global__ __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS) void k_sort_pass(Pas
   __syncthreads();
 
   // 3. rank into shared memory in digit order
-  if (!STABLE) rank_unstable<HI>(sm, k, sel, nvalid, warp, lane);
-  else if (nvalid == SORT_TILE) rank_stable<HI, true, RB>(sm, k, sel, nvalid, warp, lane);
-  else rank_stable<HI, false, RB>(sm, k, sel, nvalid, warp, lane);
+  if (!STABLE) rank_unstable<HI>(sm, k, sel, nvalid, warp, lane, a.err);
+  else if (nvalid == SORT_TILE) rank_stable<HI, true, RB>(sm, k, sel, nvalid, warp, lane, a.err);
+  else rank_stable<HI, false, RB>(sm, k, sel, nvalid, warp, lane, a.err);
 
   // 4. look-back for the global offset of each digit
   __syncthreads();
@@ -320,7 +324,8 @@ __global__ __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS) void k_sort_pass(Pas
       const int pos = i * SORT_THREADS + tid;
       if (pos < nvalid) {
         const uint64_t key = sm.keys[pos];
-        __stcs(a.out + (sm.goff[digit_of<HI>(key, sel)] + (uint64_t)pos), key);
+        const uint64_t j = sm.goff[digit_of<HI>(key, sel)] + (uint64_t)pos;
+        if (in_bounds(j, (uint64_t)a.n, a.err)) __stcs(a.out + j, key);
       }
     }
   } else {
@@ -337,12 +342,15 @@ __global__ __launch_bounds__(SORT_THREADS, SORT_MIN_BLOCKS) void k_sort_pass(Pas
         key = sm.keys[pos];
         w = (uint32_t)(key >> 32);
         const uint64_t j = sm.goff[digit_of<HI>(key, sel)] + (uint64_t)pos;
-        a.emit.adj[j + __ldg(a.emit.row_start + w)] = (int32_t)(uint32_t)key;
+        if (in_bounds(w, (uint64_t)a.emit.rows, a.err)) {
+          const uint64_t at = j + __ldg(a.emit.row_start + w);
+          if (in_bounds(at, (uint64_t)a.emit.adj_len, a.err)) a.emit.adj[at] = (int32_t)(uint32_t)key;
+        }
       }
       const uint32_t w_prev = __shfl_up_sync(FULL_MASK, w, 1);
       const uint32_t w_next = __shfl_down_sync(FULL_MASK, w, 1);
       const uint32_t starts = __ballot_sync(FULL_MASK, lane == 0 || w_prev != w);
-      if (pos < nvalid && (lane == 31 || w_next != w)) {
+      if (pos < nvalid && (lane == 31 || w_next != w) && in_bounds(w, (uint64_t)a.emit.rows, a.err)) {
         const int start = 31 - __clz(starts & le);
         atomicAdd(a.emit.count + w, lane - start + 1);
       }

@@ -146,3 +146,13 @@ def test_noalloc_binding_checks_its_arguments(lib):
         wedge.degree_offsets_noalloc(deg, off)
     with pytest.raises(ValueError, match="CUDA tensor"):
         wedge.degree_offsets_noalloc(deg.numpy(), off.numpy())
+
+
+def test_debug_build_exports_the_same_abi(lib):
+    """libwedge_debug.so (bounds-checked) loads with the same struct sizes and
+    exports exactly the symbols include/wedge.h declares."""
+    dbg = wedge.load_debug()
+    assert dbg.wedge_version() == lib.wedge_version()
+    path = os.path.join(os.path.dirname(wedge.library_path()), "libwedge_debug.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    assert set(re.findall(r"\s[TW]\s+(wedge_\w+)", out)) == set(declared_functions())
