@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -56,6 +57,14 @@ def parse():
                     help="requests per rate for the serving sweep (the full sweep uses 10000; 0 skips it)")
     ap.add_argument("--serve-rates", default="300,3000", help="arrival rates per second (full sweep: "
                                                              "100,300,1000,3000,5000)")
+    ap.add_argument("--serve-batch-samples", type=int, default=4_000_000,
+                    help="serving: samples a batch may take (a larger request goes alone)")
+    ap.add_argument("--serve-filling-samples", type=int, default=4_000_000,
+                    help="serving: a batch this large fills the GPU; two such batches do not run together")
+    ap.add_argument("--serve-queue-samples", type=int, default=500_000_000,
+                    help="serving: queued samples beyond which a submit is refused (WEDGE_EBUSY)")
+    ap.add_argument("--probe-gb", type=int, default=32,
+                    help="buffer of the random-read roofline probe, GB (much larger than L2)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched leg: the configuration the autotuner picks on this mix (thread mapping, 512 "
                          "threads, 4096-sample tiles) instead of tuning (for profiling the persistent launch)")
@@ -143,6 +152,40 @@ def oracle_step(scale: int, edgefactor: int, k: int):
     dt = time.perf_counter() - t0
     n_samples = int(r["counts"][:, 0].sum()) + int(r["glob"][0])
     return dt, adj.shape[0] // 2, n_samples
+
+
+def modelled_sampler_sectors(wedge, torch, g, b, k_bin, k_glob, hot_levels=20):
+    """The random-access model of one sample (32-byte sectors, one per
+    random access): the centre search over the stream's prefix W (uint64,
+    4 per sector, ceil(log2(len/4)) levels) + L[j] + off[v0] + adj[i], adj[j]
+    + off[v1], off[v2] + the closure search in the smaller row (int32, 8 per
+    sector, ceil(log2(d_lo/8)) levels + 1); the top `hot_levels` levels of
+    either search stay in L2. Centre searches use each stream's actual length
+    (bin sizes); the closure term uses the degrees of a recorded draw of the
+    global stream. Returns sectors per sample over the step's streams."""
+    import numpy as np
+    bi = b.info()
+    k = min(k_glob, 1 << 20)
+    rec = torch.zeros(k * 8, dtype=torch.int32, device="cuda")
+    wedge.sample(g, b, seed=SEED + 1, k_global=k, flags=wedge.FLAG_NO_BINS, records=rec)
+    r = rec.cpu().numpy().reshape(-1, 8).astype(np.int64)
+    d1, d2 = r[:, 5], r[:, 6]
+    dlo = np.minimum(d1, d2)
+    closure = np.maximum(0, np.ceil(np.log2(np.maximum(dlo, 1) / 8.0)) - hot_levels) + 1
+    per_sample = 6.0 + float(closure.mean())
+
+    def centre(length):
+        return max(0.0, math.ceil(math.log2(max(length, 1) / 4.0)) - hot_levels)
+
+    total, count = 0.0, 0
+    for bid in range(2, bi.n_bins):
+        nb = int(bi.start[bid + 1] - bi.start[bid])
+        if int(bi.p_b[bid]) > 0 and nb > 0:
+            total += k_bin * (centre(nb) + per_sample)
+            count += k_bin
+    total += k_glob * (centre(int(bi.n_wedge_vertices)) + per_sample)
+    count += k_glob
+    return total / count
 
 
 def cpu_threads():
@@ -296,7 +339,7 @@ def build_batched_mix(wedge, graphgen, torch, n_graphs=512, seed=3):
     return items, edges
 
 
-def bench_batched(wedge, graphgen, torch, probe_rate=None, probe_spa=None, autotune=True):
+def bench_batched(wedge, graphgen, torch, probe_rate=None, probe_spa=None, autotune=True, probe_l2=None):
     """512 plain wedge_sample calls vs one autotuned persistent launch; the
     persistent launch's random-access roofline fraction where DRAM sector
     counters of that kernel on this mix exist for the current source."""
@@ -349,14 +392,24 @@ def bench_batched(wedge, graphgen, torch, probe_rate=None, probe_spa=None, autot
     for it in items:
         it["bins"].free()
         it["graph"].free()
-    roof = {"bound": "random-sector", "kernel": "batch_sample", "achieved": None, "peak": None, "frac": None,
-            "dram_sectors_per_sample": None}
+    # Every graph of the mix has at most 2^22 vertices, so in the access model
+    # (modelled_sampler_sectors) all search levels stay in L2: 7 random
+    # accesses per sample (6 gathers + the last closure probe), and most of
+    # the mix's working set is L2-resident (ncu: a few DRAM sectors per
+    # sample). The ceiling is then the rate of random reads that hit L2.
+    s_mix = 7.0
+    roof = {"bound": "random-access (L2-resident working set)", "kernel": "batch_sample",
+            "modelled_accesses_per_sample": s_mix, "unit": "G accesses/s",
+            "achieved": s_mix * samples / batch_s / 1e9,
+            "peak": probe_l2 / 1e9 if probe_l2 else None,
+            "frac": s_mix * samples / batch_s / probe_l2 if probe_l2 else None,
+            "peak_source": "wedge_probe_random_read live over a 64 MB buffer (L2-resident), best of 3"}
     ent = ncu_figures("batch_sample")
     if ent and ent.get("samples") == samples and probe_rate and probe_spa:
         spl = ent["dram_sectors_per_sample"]
-        roof.update(dram_sectors_per_sample=spl, achieved=spl * samples / batch_s * 32 / 1e9,
-                    peak=probe_rate * probe_spa * 32 / 1e9, unit="GB/s")
-        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["dram"] = {"dram_sectors_per_sample": spl, "achieved_gbs": spl * samples / batch_s * 32 / 1e9,
+                        "dram_random_peak_gbs": probe_rate * probe_spa * 32 / 1e9,
+                        "frac": spl * samples / batch_s / (probe_rate * probe_spa)}
     return {"workload": "512 graphs: 256 Kronecker (scale log-uniform 8-22) + 256 Chung-Lu (exponent 2.0-2.6, "
                         "mean degree 8-64, 2^10-2^22 vertices); per-bin and global budgets log-uniform 1e3-1e6",
             "graphs": len(items), "generated_edges": edges, "samples": samples,
@@ -368,7 +421,8 @@ def bench_batched(wedge, graphgen, torch, probe_rate=None, probe_spa=None, autot
             "persistent_grid": info["grid"], "setup_s": setup_s, "tune_s": tune_s, "roofline": roof}
 
 
-def bench_serving(wedge, graphgen, torch, rates, n_requests, n_graphs=64, seed=5, upload_frac=0.01):
+def bench_serving(wedge, graphgen, torch, rates, n_requests, n_graphs=64, seed=5, upload_frac=0.01,
+                  batch_samples=4_000_000, filling_samples=4_000_000, queue_samples=500_000_000):
     """Poisson request stream against a resident pool of Kronecker and
     Chung-Lu graphs (scales 14-24) under a 150 GB HBM budget; per-request eps
     drawn from {0.01, 0.005, 0.002}, delta 0.001; 1% of arrivals upload a new
@@ -399,11 +453,11 @@ def bench_serving(wedge, graphgen, torch, rates, n_requests, n_graphs=64, seed=5
         return s, d, n
 
     # Admission: at most ~50 ms of queued work at the GPU's ~10 Gwedges/s;
-    # batches capped at ~6 ms of work; one GPU-filling batch at a time.
+    # batches capped at 4M samples (~0.5 ms of work); one GPU-filling batch at a time.
     srv = wedge.Server(hbm_budget_bytes=150 * 10**9, slots=2,
                        launch={"block_threads": 512, "samples_per_tile": 4096, "flags": wedge.BATCH_DIRECT},
-                       max_batch_samples=64_000_000, max_queued_samples=500_000_000,
-                       gpu_filling_samples=2_000_000)
+                       max_batch_samples=batch_samples, max_queued_samples=queue_samples,
+                       gpu_filling_samples=filling_samples)
     ids, plain = [], []
     for i in range(n_graphs):
         s, d, n = gen_edges(i)
@@ -498,9 +552,10 @@ def bench_serving(wedge, graphgen, torch, rates, n_requests, n_graphs=64, seed=5
     return {"workload": f"{n_graphs} resident graphs (half Kronecker, half Chung-Lu, scales 14-24) under a 150 GB "
                         f"budget; Poisson arrivals; eps in {{0.01, 0.005, 0.002}}, delta 0.001; "
                         f"{upload_frac:.0%} uploads",
-            "policy": "batches in arrival order up to 64M samples; one GPU-filling (>= 2M samples) batch at a time, "
-                      "smaller requests overtake queued large ones; submits refused (WEDGE_EBUSY) past 500M queued "
-                      "samples; latency percentiles over admitted requests",
+            "policy": f"batches in arrival order up to {batch_samples:,} samples; one GPU-filling "
+                      f"(>= {filling_samples:,} samples) batch at a time, smaller requests overtake queued large "
+                      f"ones; submits refused (WEDGE_EBUSY) past {queue_samples:,} queued samples; latency "
+                      f"percentiles over admitted requests",
             "resident_bytes": res_bytes, "rates": out}
 
 
@@ -586,6 +641,7 @@ def compact_summary(value, ms_step, gwps, roofline, sampling_roofline, e2e, batc
     out = {"s_per_Medge": value, "ms_per_step": r(ms_step, 2), "gwedges_checked_per_s": r(gwps, 3),
            "sort_pass_frac_of_copy_peak": r(roofline["frac"], 3),
            "sampler_frac_of_random_access_peak": r(sampling_roofline.get("frac"), 3),
+           "sampler_modelled_sectors_per_sample": r(sampling_roofline.get("modelled_sectors_per_sample"), 2),
            "e2e_ms_per_step": r(e2e.get("ms_per_step"), 1) if e2e else None,
            "e2e_h2d_link_gbs": r(e2e.get("h2d_link_gbs"), 1) if e2e else None}
     if batched:
@@ -715,19 +771,39 @@ def run_ours(args):
     # random reads can move sectors on this GPU. Random reads are probed live
     # (accesses/s); sectors per sample and per probe access come from ncu
     # counters taken on the current kernel sources (null otherwise).
+    # Model of the sampler's random accesses on this graph (sectors per sample).
+    g_m = wedge.graph_build(src, dst, n)
+    b_m = wedge.bin(g_m, tau=TAU, omega=OMEGA)
+    s_alg = modelled_sampler_sectors(wedge, torch, g_m, b_m, K_SAMPLES, K_SAMPLES)
+    b_m.free()
+    g_m.free()
     wedge.trim()
-    probe = wedge.probe_random_read(32 << 30, 1 << 30)
+    probe = wedge.probe_random_read(args.probe_gb << 30, 1 << 30)
+    probe_l2 = wedge.probe_random_read(64 << 20, 1 << 30)  # random reads that hit L2
     sent, pent = ncu_figures("sample_closure"), ncu_figures("probe_random_read")
-    spl = sent["dram_sectors_per_sample"] if (sent and sent.get("scale") == scale) else None
     spa = pent["dram_sectors_per_access"] if pent else None
-    ach = spl * info["samples"] / (samp_ms / 1e3) * 32 if (spl and samp_ms > 0) else None
-    peak = probe * spa * 32 if spa else None
-    sampling_roofline = {"bound": "random-sector", "kernel": "sample_closure", "unit": "GB/s",
-                         "achieved": ach / 1e9 if ach else None, "peak": peak / 1e9 if peak else None,
-                         "frac": ach / peak if (ach and peak) else None, "dram_sectors_per_sample": spl,
+    rate = info["samples"] / (samp_ms / 1e3) if samp_ms > 0 else None
+    # Algorithmic roofline: the model's random accesses per second against the
+    # probe's independent random reads per second (one sector each).
+    sampling_roofline = {"bound": "random-access", "kernel": "sample_closure", "unit": "G accesses/s",
+                         "modelled_sectors_per_sample": s_alg,
+                         "achieved": s_alg * rate / 1e9 if rate else None, "peak": probe / 1e9,
+                         "frac": s_alg * rate / probe if rate else None,
                          "probe_accesses_per_s": probe, "probe_dram_sectors_per_access": spa,
-                         "peak_source": "wedge_probe_random_read live (2^30 independent 4-byte reads over 32 GB, "
-                                        "best of 3) x DRAM sectors per access from ncu"}
+                         "probe_l2_accesses_per_s": probe_l2,
+                         "peak_source": f"wedge_probe_random_read live (2^30 independent 4-byte reads over "
+                                        f"{args.probe_gb} GB, best of 3)"}
+    if sent and spa:
+        # DRAM sectors per sample measured by ncu on a smaller graph of the same
+        # family, beside the model's sectors at that size x the DRAM sectors one
+        # random access moves
+        sampling_roofline["measured"] = {
+            "scale": sent.get("scale"), "dram_sectors_per_sample": sent["dram_sectors_per_sample"],
+            "modelled_sectors_per_sample_at_that_scale": sent.get("modelled_sectors_per_sample"),
+            "modelled_dram_sectors_per_sample_at_that_scale":
+                sent["modelled_sectors_per_sample"] * spa if sent.get("modelled_sectors_per_sample") else None}
+        if sent.get("scale") == scale:
+            sampling_roofline["dram_frac"] = sent["dram_sectors_per_sample"] * rate / (probe * spa) if rate else None
 
     # e2e: the same step from pinned host buffers through the C ABI, each step
     # timed on its own (the host link is shared with the node's other tenants).
@@ -851,7 +927,8 @@ def run_ours(args):
         wedge.trim()
         torch.cuda.empty_cache()
         serving = bench_serving(wedge, graphgen, torch, [float(r) for r in args.serve_rates.split(",")],
-                                args.serve_requests)
+                                args.serve_requests, batch_samples=args.serve_batch_samples,
+                                filling_samples=args.serve_filling_samples, queue_samples=args.serve_queue_samples)
         wedge.trim()
 
     batched = None
@@ -859,7 +936,7 @@ def run_ours(args):
         wedge.trim()
         torch.cuda.empty_cache()
         batched = bench_batched(wedge, graphgen, torch, probe_rate=probe, probe_spa=spa,
-                                autotune=not args.no_autotune)
+                                autotune=not args.no_autotune, probe_l2=probe_l2)
         wedge.trim()
 
     cpu = None

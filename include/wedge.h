@@ -108,6 +108,22 @@ WEDGE_API wedge_status wedge_graph_get_info(const wedge_graph* g, wedge_graph_in
  * off[n_vertices + 1], adj[n_adj], deg[n_vertices]. Synchronises s. */
 WEDGE_API wedge_status wedge_graph_copy(const wedge_graph* g, int64_t* off, int32_t* adj, int32_t* deg, wedge_stream s);
 
+/* Checkpoint / resume of the graph handle (the paper's phases restart from
+ * their HDFS outputs; here a built CSR is saved with wedge_graph_copy and
+ * later made a graph again without the sort): a new graph from a CSR in
+ * host or device memory, copied into library-owned device memory. One kernel
+ * checks it and derives the degrees: off (n_vertices + 1 int64) rises from
+ * 0 to n_adj, every row of adj (n_adj int32) is strictly ascending with
+ * ids in [0, n_vertices) and no self-loop. Symmetry is the caller's promise
+ * (a CSR saved from wedge_graph_build has it) and is not checked. Bins are
+ * rebuilt with wedge_bin; sampling resumes from any sample index with
+ * wedge_sample_params.first_sample. The caller keeps its arrays; they are
+ * not retained. Synchronises s.
+ * Errors: EINVAL (NULL, n_vertices < 1, odd or negative n_adj, a row or
+ * offset check failed; nothing is returned), ENOMEM, ECUDA. */
+WEDGE_API wedge_status wedge_graph_from_csr(const int64_t* off, const int32_t* adj, int32_t n_vertices, int64_t n_adj,
+                                            wedge_stream s, wedge_graph** out);
+
 /* --------------------------------------------------------------------------
  * Bins: degree bins (Sec. 4.2) and per-bin wedge totals (Alg. Phase 1b).
  *
@@ -343,7 +359,10 @@ WEDGE_API wedge_status wedge_autotune(const wedge_request* reqs, int n_reqs, wed
  * and only smaller requests, taken from anywhere in the queue in arrival
  * order, fill the free slot, so small requests never queue behind two large
  * ones sharing the GPU. So requests that arrive while others run are
- * admitted as slots free up and overlap with them on the GPU.
+ * admitted as slots free up and overlap with them on the GPU. The sampling
+ * streams are created at the device's highest stream priority and the build
+ * stream at its lowest, so a sampling batch launched during an upload gets
+ * the next free SMs ahead of the build's remaining CTAs.
  * wedge_server_wait blocks until a ticket's request is
  * done and returns its counts, which equal wedge_sample's for the same
  * parameters (the mix never changes a result), and its timing. Thread-safe;

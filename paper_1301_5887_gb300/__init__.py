@@ -172,7 +172,8 @@ EXPORTS = ["wedge_status_str", "wedge_last_error", "wedge_version", "wedge_abi_s
            "wedge_batch_free", "wedge_batch_info", "wedge_sample_batch", "wedge_autotune", "wedge_server_create",
            "wedge_server_destroy", "wedge_server_add_graph", "wedge_server_remove_graph", "wedge_server_submit",
            "wedge_server_wait", "wedge_server_stats", "wedge_probe_random_read", "wedge_triangle_stats",
-           "wedge_exact", "wedge_pool_used_bytes", "wedge_test_fail_allocation", "wedge_test_lookback_timeout"]
+           "wedge_exact", "wedge_pool_used_bytes", "wedge_test_fail_allocation", "wedge_test_lookback_timeout",
+           "wedge_graph_from_csr"]
 
 _lib = None
 
@@ -255,6 +256,7 @@ def _configure(lib):
         "wedge_pool_used_bytes": ([], u64),
         "wedge_test_fail_allocation": ([i64], None),
         "wedge_test_lookback_timeout": ([u32, P], st),
+        "wedge_graph_from_csr": ([P, P, i32, i64, P, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -552,6 +554,32 @@ def force_lookback_timeout(spin_limit: int, stream=None):
     """Test hook: a scan whose look-back waits on a status word nothing sets,
     with the poll limit lowered to spin_limit; raises WedgeError(ETIMEOUT)."""
     _check(load().wedge_test_lookback_timeout(int(spin_limit), _stream_handle(stream)))
+
+
+def graph_from_csr(off, adj, n_vertices: int, stream=None) -> "Graph":
+    """A graph from a saved CSR (host or device arrays; wedge_graph_from_csr)."""
+    lib = load()
+    po, ko = _ptr(off, np.int64)
+    pa, ka = _ptr(adj, np.int32)
+    n_adj = int(ka.shape[0]) if hasattr(ka, "shape") else int(ka.numel())
+    if int(ko.shape[0]) != int(n_vertices) + 1:
+        raise ValueError("off must hold n_vertices + 1 entries")
+    h = ctypes.c_void_p()
+    _check(lib.wedge_graph_from_csr(po, pa if n_adj else None, int(n_vertices), n_adj, _stream_handle(stream),
+                                    ctypes.byref(h)))
+    return Graph(h.value)
+
+
+def graph_save(graph: "Graph", path: str):
+    """Save a graph's CSR to a .npz file (checkpoint; reload with graph_load)."""
+    off, adj, _ = graph.csr_numpy()
+    np.savez(path, off=off, adj=adj, n_vertices=np.int64(off.shape[0] - 1))
+
+
+def graph_load(path: str, stream=None) -> "Graph":
+    """A graph from a file written by graph_save (validated on the device)."""
+    z = np.load(path)
+    return graph_from_csr(z["off"], z["adj"], int(z["n_vertices"]), stream=stream)
 
 
 def hoeffding_k(eps: float, delta: float) -> int:

@@ -138,12 +138,13 @@ __device__ __forceinline__ uint32_t load_unique(const uint64_t* __restrict__ key
 
 // Adjacent-unique of sorted forward keys (u, w): forward row lengths, the
 // transposed keys (w << 32) | u of the unique keys in order, with the digit
-// histograms of their `tpasses` low bytes of w, and per tile the number of
-// unique keys in earlier tiles (tile_excl), from which k_place_fwd later
-// recovers every unique key's index.
+// histograms of their TP low bytes of w, and per tile the number of unique
+// keys in earlier tiles (tile_excl), from which k_place_fwd later recovers
+// every unique key's index.
+template <int TP>
 __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_dedup(const uint64_t* __restrict__ keys, int64_t nkeys, uint32_t b,
                                                          int32_t n, uint64_t sentinel, uint64_t* __restrict__ tkeys,
-                                                         int tpasses, unsigned long long* __restrict__ thist,
+                                                         unsigned long long* __restrict__ thist,
                                                          int32_t* __restrict__ fdeg, uint64_t* __restrict__ tile_excl,
                                                          uint64_t* status, uint32_t* tile_ctr, uint32_t* err,
                                                          int64_t* n_unique, int64_t prefetch_tiles) {
@@ -190,7 +191,8 @@ __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_dedup(const uint64_t* __re
     }
     if ((bal[i] >> lane) & 1u) {
       const uint32_t w = (uint32_t)(k[i] & vmask);
-      for (int p = 0; p < tpasses; ++p) atomicAdd(&s_hist[p * 256 + ((w >> (8 * p)) & 255u)], 1u);
+#pragma unroll
+      for (int p = 0; p < TP; ++p) atomicAdd(&s_hist[p * 256 + __byte_perm(w, 0u, 0x4440u | p)], 1u);
     }
   }
   if (warp == 0) {
@@ -217,7 +219,7 @@ __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_dedup(const uint64_t* __re
     }
     pos += __popc(bal[i]);
   }
-  for (int i = tid; i < tpasses * 256; i += DEDUP_THREADS)
+  for (int i = tid; i < TP * 256; i += DEDUP_THREADS)
     if (s_hist[i]) atomicAdd(&thist[i], (unsigned long long)s_hist[i]);
 }
 
@@ -313,6 +315,37 @@ __global__ __launch_bounds__(256) void k_place_back(const uint64_t* __restrict__
     const uint64_t dst = j + __ldg(foff + (key >> 32));
     if (in_bounds(dst, (uint64_t)adj_len, err)) adj[dst] = (int32_t)(uint32_t)key;
   }
+}
+
+// Check of an imported CSR, one thread per row: the offsets rise from 0 to
+// n_adj, each row is strictly ascending with entries in [0, n) other than
+// the row's own vertex; degrees and the largest degree come out on the way.
+__global__ __launch_bounds__(256) void k_check_rows(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                                                    int32_t n, int64_t n_adj, int32_t* __restrict__ deg,
+                                                    int32_t* maxdeg, uint32_t* err) {
+  int32_t mx = 0;
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+    const int64_t o0 = off[x], o1 = off[x + 1];
+    if ((x == 0 && o0 != 0) || o0 < 0 || o1 < o0 || o1 > n_adj || o1 - o0 >= (int64_t(1) << 31)) {
+      bad = true;
+      deg[x] = 0;
+      continue;
+    }
+    int32_t prev = -1;
+    for (int64_t i = o0; i < o1 && !bad; ++i) {
+      const int32_t v = adj[i];
+      bad = v <= prev || v >= n || v == (int32_t)x;
+      prev = v;
+    }
+    deg[x] = (int32_t)(o1 - o0);
+    mx = max(mx, (int32_t)(o1 - o0));
+  }
+  if (bad) atomicOr(err, DERR_BAD_ID);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(FULL_MASK, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(maxdeg, mx);
 }
 
 int grid_stride_blocks(int64_t items, int threads) {
@@ -585,9 +618,21 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     // L2 prefetch one SM count of tiles ahead, where the sorted keys are aligned
     const int64_t key_prefetch = (reinterpret_cast<uintptr_t>(sorted) & 15) == 0 ? sm_count() : 0;
     st = launch("dedup_rows", s, [&] {
-      k_dedup<<<(unsigned)tiles, DEDUP_THREADS, 0, s>>>(sorted, n_edges, b, n_vertices, sentinel, tkeys, tpasses,
-                                                        sort_hist_area(bb.scratch), bb.fdeg, bb.tile_excl, status,
-                                                        ctr, bb.derr, bb.scalars, key_prefetch);
+      unsigned long long* th = sort_hist_area(bb.scratch);
+      const unsigned grid = (unsigned)tiles;
+      // the transposed sort runs over the ceil(b/8) <= 4 low bytes of w
+      if (tpasses <= 1)
+        k_dedup<1><<<grid, DEDUP_THREADS, 0, s>>>(sorted, n_edges, b, n_vertices, sentinel, tkeys, th, bb.fdeg,
+                                                  bb.tile_excl, status, ctr, bb.derr, bb.scalars, key_prefetch);
+      else if (tpasses == 2)
+        k_dedup<2><<<grid, DEDUP_THREADS, 0, s>>>(sorted, n_edges, b, n_vertices, sentinel, tkeys, th, bb.fdeg,
+                                                  bb.tile_excl, status, ctr, bb.derr, bb.scalars, key_prefetch);
+      else if (tpasses == 3)
+        k_dedup<3><<<grid, DEDUP_THREADS, 0, s>>>(sorted, n_edges, b, n_vertices, sentinel, tkeys, th, bb.fdeg,
+                                                  bb.tile_excl, status, ctr, bb.derr, bb.scalars, key_prefetch);
+      else
+        k_dedup<4><<<grid, DEDUP_THREADS, 0, s>>>(sorted, n_edges, b, n_vertices, sentinel, tkeys, th, bb.fdeg,
+                                                  bb.tile_excl, status, ctr, bb.derr, bb.scalars, key_prefetch);
     });
     if (st != WEDGE_OK) return bail(st);
     int64_t m_unique = 0;
@@ -688,5 +733,62 @@ extern "C" wedge_status wedge_graph_copy(const wedge_graph* g, int64_t* off, int
     WEDGE_CUDA_TRY(cudaMemcpyAsync(deg, g->deg, (size_t)g->n * sizeof(int32_t), cudaMemcpyDefault, s),
                    "wedge_graph_copy");
   WEDGE_CUDA_TRY(cudaStreamSynchronize(s), "wedge_graph_copy");
+  return WEDGE_OK;
+}
+
+extern "C" wedge_status wedge_graph_from_csr(const int64_t* off, const int32_t* adj, int32_t n_vertices, int64_t n_adj,
+                                             wedge_stream stream, wedge_graph** out) {
+  clear_error();
+  if (!out) return fail(WEDGE_EINVAL, "wedge_graph_from_csr: out is NULL");
+  *out = nullptr;
+  if (n_vertices < 1 || n_adj < 0 || !off || (n_adj > 0 && !adj))
+    return fail(WEDGE_EINVAL, "wedge_graph_from_csr: bad sizes or NULL arrays");
+  if (n_adj % 2) return fail(WEDGE_EINVAL, "wedge_graph_from_csr: a symmetric CSR has an even n_adj");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  wedge_graph* g = new wedge_graph();
+  cudaGetDevice(&g->device);
+  g->uid = next_uid();
+  g->n = n_vertices;
+  g->id_bits = id_bits_for(n_vertices);
+  g->n_adj = n_adj;
+  g->n_input = n_adj / 2;
+  g->off = nullptr;
+  g->adj = nullptr;
+  g->deg = nullptr;
+  uint32_t* derr = nullptr;
+  auto bail = [&](wedge_status e) {
+    dfree(derr, s);
+    free_graph(g, s);
+    return e;
+  };
+  wedge_status st;
+  if ((st = dalloc_n(&g->off, (size_t)n_vertices + 1, s, "wedge_graph_from_csr")) != WEDGE_OK) return bail(st);
+  if ((st = dalloc_n(&g->deg, (size_t)n_vertices, s, "wedge_graph_from_csr")) != WEDGE_OK) return bail(st);
+  if ((st = dalloc_n(&g->adj, (size_t)(n_adj > 0 ? n_adj : 1), s, "wedge_graph_from_csr")) != WEDGE_OK) return bail(st);
+  if ((st = dalloc_n(&derr, 2, s, "wedge_graph_from_csr")) != WEDGE_OK) return bail(st);
+  cudaError_t e = cudaMemcpyAsync(g->off, off, ((size_t)n_vertices + 1) * sizeof(int64_t), cudaMemcpyDefault, s);
+  if (e == cudaSuccess && n_adj > 0)
+    e = cudaMemcpyAsync(g->adj, adj, (size_t)n_adj * sizeof(int32_t), cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, 2 * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "wedge_graph_from_csr"));
+  int32_t* maxdeg = reinterpret_cast<int32_t*>(derr + 1);
+  st = launch("check_rows", s, [&] {
+    k_check_rows<<<grid_stride_blocks(n_vertices, 256), 256, 0, s>>>(g->off, g->adj, n_vertices, n_adj, g->deg, maxdeg,
+                                                                      derr);
+  });
+  if (st != WEDGE_OK) return bail(st);
+  uint32_t h[2] = {0, 0};
+  int64_t last = 0;
+  e = cudaMemcpyAsync(h, derr, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&last, g->off + n_vertices, sizeof(last), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "wedge_graph_from_csr"));
+  if ((h[0] & DERR_BAD_ID) || last != n_adj)
+    return bail(fail(WEDGE_EINVAL, "wedge_graph_from_csr: not a CSR of ascending rows with ids in [0, %d), no "
+                                   "self-loops and off[n] = n_adj",
+                     n_vertices));
+  g->max_degree = (int32_t)h[1];
+  dfree(derr, s);
+  *out = g;
   return WEDGE_OK;
 }

@@ -290,9 +290,16 @@ extern "C" wedge_status wedge_server_create(const wedge_server_config* cfg, wedg
   if (sv->cfg.tau == 0) sv->cfg.tau = 1;
   if (sv->cfg.omega == 0) sv->cfg.omega = 2;
   cudaGetDevice(&sv->device);
+  // Sampling streams take the device's highest priority and the upload
+  // stream its lowest: while an upload builds, the block scheduler starts a
+  // waiting sampling CTA before the next build CTA (running CTAs are never
+  // preempted; the build's look-back waits are on tiles taken by ticket, so
+  // they are already running and finish).
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   for (uint32_t s = 0; s < sv->cfg.slots; ++s) {
     cudaStream_t st = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaError_t e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio_greatest);
     if (e != cudaSuccess) {
       for (cudaStream_t x : sv->streams) cudaStreamDestroy(x);
       delete sv;
@@ -301,7 +308,7 @@ extern "C" wedge_status wedge_server_create(const wedge_server_config* cfg, wedg
     sv->streams.push_back(st);
     sv->slot_busy.push_back(false);
   }
-  cudaError_t e = cudaStreamCreateWithFlags(&sv->build_stream, cudaStreamNonBlocking);
+  cudaError_t e = cudaStreamCreateWithPriority(&sv->build_stream, cudaStreamNonBlocking, prio_least);
   if (e != cudaSuccess) {
     for (cudaStream_t x : sv->streams) cudaStreamDestroy(x);
     delete sv;

@@ -122,3 +122,18 @@ def test_scale28_full_size():
         jj = jp + (1 if jp >= i else 0)
         assert v1 == int(row0[i]) and v2 == int(row0[jj])
         assert bool(closed) == bool(np.isin(v2, rows[v1]))
+
+    # (c) every tally of the step against the oracle's sampler on the same CSR
+    # (downloaded to the host: 36 GB), the oracle timed as the partial CPU
+    # baseline at this size (sampling only; its CSR build does not fit the host)
+    import time
+    off_h = off.cpu().numpy()
+    adj_h = np.empty(int(gi.n_adj), np.int32)
+    g.copy(adj=adj_h)
+    t0 = time.perf_counter()
+    ref = oracle.sample(off_h, adj_h, 1, 2, SEED, K, K)
+    dt = time.perf_counter() - t0
+    print(f"oracle sampling at scale 28 on the host: {dt:.2f} s for {2 * K + K * (bi.n_bins - 2)} samples at most")
+    assert np.array_equal(c.counts_matrix(), ref["counts"])
+    assert c.k_global == int(ref["glob"][0]) and c.closed_global == int(ref["glob"][1])
+    assert np.array_equal(c.stats, ref["stats"])
