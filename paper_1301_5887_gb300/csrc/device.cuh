@@ -139,7 +139,7 @@ __device__ __forceinline__ uint64_t lookback_window(const uint64_t* status, int6
 // that have only published aggregates costs one round trip per 32 tiles
 // instead of one per tile. Same result on every lane. Bounded like lookback().
 __device__ __forceinline__ uint64_t lookback_warp(const uint64_t* status, int64_t tile, uint32_t epoch, uint32_t* err,
-                                                  int lane) {
+                                                  int lane, uint32_t spin_limit = SPIN_LIMIT) {
   uint64_t excl = 0;
   int64_t hi = tile - 1;  // nearest predecessor not yet summed
   uint32_t spins = 0;
@@ -168,7 +168,7 @@ __device__ __forceinline__ uint64_t lookback_warp(const uint64_t* status, int64_
     if (first_inc < first_wait) break;  // reached an inclusive prefix
     hi -= take;
     if (take == 0) {
-      if (++spins >= SPIN_LIMIT) {
+      if (++spins >= spin_limit) {
         if (lane == 0) atomicOr(err, DERR_TIMEOUT);
         break;
       }

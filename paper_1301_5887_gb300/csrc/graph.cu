@@ -50,7 +50,9 @@ __device__ __forceinline__ void count_digits(uint32_t* sh, uint64_t key, int pas
 }
 
 // Expand edges to packed keys and accumulate the radix sort's digit
-// histograms (8-bit digits, `passes` of them) in shared memory on the way.
+// histograms (8-bit digits, `passes` of them) in shared memory on the way;
+// each CTA adds them to `hist` (this sort's) and to `hist_total` (every
+// forward key of the build, over all groups of a host edge list).
 // VEC: src, dst and keys are 16-byte aligned, and each thread takes four
 // edges per step with 16-byte loads (the scalar form keeps too few bytes in
 // flight to stream at the HBM rate). WRITE false: histograms only (the sort's
@@ -59,7 +61,7 @@ template <bool VEC, bool WRITE>
 __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                                                 int64_t m, int32_t n, uint32_t b, uint64_t sentinel, int passes,
                                                 uint64_t* __restrict__ keys, unsigned long long* __restrict__ hist,
-                                                uint32_t* err) {
+                                                unsigned long long* __restrict__ hist_total, uint32_t* err) {
   __shared__ uint32_t sh[SORT_MAX_PASSES * 256];
   for (int i = threadIdx.x; i < SORT_MAX_PASSES * 256; i += blockDim.x) sh[i] = 0;
   __syncthreads();
@@ -93,7 +95,26 @@ __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src,
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
-    if (sh[i]) atomicAdd(&hist[i], (unsigned long long)sh[i]);
+    if (sh[i]) {
+      atomicAdd(&hist[i], (unsigned long long)sh[i]);
+      atomicAdd(&hist_total[i], (unsigned long long)sh[i]);
+    }
+}
+
+// Digit histograms of the transposed sort (the tp low bytes of w, the larger
+// endpoint) over every forward key (u << b) | w: byte p of w is the forward
+// key's digit p where 8p + 8 <= b, and the top byte, with b - 8p < 8
+// significant bits, is that digit folded over u's bits above them. Dedup
+// then subtracts the keys that are not unique forward edges (duplicates and
+// self-loop sentinels). One CTA of 256 threads per byte.
+__global__ __launch_bounds__(256) void k_trans_hist(const unsigned long long* __restrict__ fwd, uint32_t b,
+                                                    unsigned long long* __restrict__ thist) {
+  const uint32_t p = blockIdx.x, x = threadIdx.x;
+  const uint32_t bits = min(8u, b - 8u * p);
+  unsigned long long v = 0;
+  if (x < (1u << bits))
+    for (uint32_t y = 0; y < (256u >> bits); ++y) v += fwd[p * 256 + (x | (y << bits))];
+  thist[p * 256 + x] = v;
 }
 
 // Ask L2 to prefetch dedup tile `t` of the sorted keys (a whole tile, in
@@ -137,10 +158,12 @@ __device__ __forceinline__ uint32_t load_unique(const uint64_t* __restrict__ key
 }
 
 // Adjacent-unique of sorted forward keys (u, w): forward row lengths, the
-// transposed keys (w << 32) | u of the unique keys in order, with the digit
-// histograms of their TP low bytes of w, and per tile the number of unique
-// keys in earlier tiles (tile_excl), from which k_place_fwd later recovers
-// every unique key's index.
+// transposed keys (w << 32) | u of the unique keys in order, and per tile the
+// number of unique keys in earlier tiles (tile_excl), from which k_place_fwd
+// later recovers every unique key's index. thist holds the digit histograms
+// of the TP low bytes of w over every forward key (k_trans_hist); the keys
+// dropped here (duplicates, sentinels) are counted and subtracted, which
+// leaves the histograms of the transposed keys.
 template <int TP>
 __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_dedup(const uint64_t* __restrict__ keys, int64_t nkeys, uint32_t b,
                                                          int32_t n, uint64_t sentinel, uint64_t* __restrict__ tkeys,
@@ -189,7 +212,7 @@ __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_dedup(const uint64_t* __re
       const uint32_t c = __popc(bal[i] & le & ~((1u << start) - 1u));
       if (c) atomicAdd(fdeg + u, (int32_t)c);
     }
-    if ((bal[i] >> lane) & 1u) {
+    if (!((bal[i] >> lane) & 1u) && wbase + i * 32 + lane < nkeys) {  // a key dropped here
       const uint32_t w = (uint32_t)(k[i] & vmask);
 #pragma unroll
       for (int p = 0; p < TP; ++p) atomicAdd(&s_hist[p * 256 + __byte_perm(w, 0u, 0x4440u | p)], 1u);
@@ -220,7 +243,7 @@ __global__ __launch_bounds__(DEDUP_THREADS, 3) void k_dedup(const uint64_t* __re
     pos += __popc(bal[i]);
   }
   for (int i = tid; i < TP * 256; i += DEDUP_THREADS)
-    if (s_hist[i]) atomicAdd(&thist[i], (unsigned long long)s_hist[i]);
+    if (s_hist[i]) atomicAdd(&thist[i], 0ULL - (unsigned long long)s_hist[i]);
 }
 
 // Backward row lengths: runs of equal w in the sorted transposed keys; the
@@ -368,6 +391,7 @@ struct BuildBuffers {
   void* scratch = nullptr;
   uint32_t* derr = nullptr;     // [0] error bits, then padding
   int64_t* scalars = nullptr;   // [0] unique undirected edges, [1] max degree (int32 in low half)
+  unsigned long long* fhist = nullptr;  // forward digit histograms over every key of the build
   ~BuildBuffers() {
     dfree(keys_a, s);
     dfree(keys_b, s);
@@ -378,6 +402,7 @@ struct BuildBuffers {
     dfree(scratch, s);
     dfree(derr, s);
     dfree(scalars, s);
+    dfree(fhist, s);
   }
 };
 
@@ -518,7 +543,11 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
         std::max(std::max(sort_scratch_bytes(n_edges, 2 * (int)b), merge_scratch_bytes(n_edges)),
                  std::max(scan_scratch_bytes(n_edges), scan_scratch_bytes(n_vertices) + hist_bytes));
     if ((st = dalloc(&bb.scratch, scratch_bytes, s, "wedge_graph_build: scratch")) != WEDGE_OK) return bail(st);
+    if ((st = dalloc_n(&bb.fhist, SORT_MAX_PASSES * 256, s, "wedge_graph_build: histograms")) != WEDGE_OK)
+      return bail(st);
     BUILD_TRY(cudaMemsetAsync(bb.fdeg, 0, 2 * (size_t)n_vertices * sizeof(int32_t), s), "wedge_graph_build");
+    BUILD_TRY(cudaMemsetAsync(bb.fhist, 0, SORT_MAX_PASSES * 256 * sizeof(unsigned long long), s),
+              "wedge_graph_build");
 
     // 1-2. the forward sort's digit histograms, then the sort, whose first
     //     pass computes the forward keys from the edges (a one-edge list is
@@ -535,16 +564,16 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
       return launch(write ? "expand_edges" : "edge_histograms", s, [&] {
         if (vec && write)
           k_expand<true, true><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out, hist,
-                                                    bb.derr);
+                                                    bb.fhist, bb.derr);
         else if (vec)
           k_expand<true, false><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out, hist,
-                                                     bb.derr);
+                                                     bb.fhist, bb.derr);
         else if (write)
           k_expand<false, true><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out, hist,
-                                                     bb.derr);
+                                                     bb.fhist, bb.derr);
         else
           k_expand<false, false><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out, hist,
-                                                      bb.derr);
+                                                      bb.fhist, bb.derr);
       });
     };
     // sort of `len` edges from s_in/d_in into keys_a/keys_b at e0
@@ -619,6 +648,7 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
     const int64_t key_prefetch = (reinterpret_cast<uintptr_t>(sorted) & 15) == 0 ? sm_count() : 0;
     st = launch("dedup_rows", s, [&] {
       unsigned long long* th = sort_hist_area(bb.scratch);
+      k_trans_hist<<<tpasses, 256, 0, s>>>(bb.fhist, b, th);
       const unsigned grid = (unsigned)tiles;
       // the transposed sort runs over the ceil(b/8) <= 4 low bytes of w
       if (tpasses <= 1)

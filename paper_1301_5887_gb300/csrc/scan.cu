@@ -4,9 +4,10 @@
 //
 // One CTA scans a tile of 4096 items: a warp-striped coalesced load into
 // shared memory, a per-thread sequential sum over 16 consecutive items, a
-// block scan of thread sums, then one look-back by thread 0 to get the
-// tile's global prefix. Tiles are claimed in launch order from an atomic
-// ticket, so every wait is on a tile that is already running.
+// block scan of thread sums, then a look-back by warp 0 (32 predecessors per
+// round trip) to get the tile's global prefix. Tiles are claimed in launch
+// order from an atomic ticket, so every wait is on a tile that is already
+// running; each CTA asks L2 to prefetch the tile one wave of CTAs ahead.
 #include <mutex>
 
 #include "device.cuh"
@@ -28,7 +29,8 @@ template <typename Tin, typename Tout, bool CHECK = false>
 __global__ __launch_bounds__(SCAN_THREADS) void k_scan_excl(const Tin* __restrict__ in, Tout* __restrict__ out,
                                                             int64_t n, uint64_t* status, uint32_t* tile_ctr,
                                                             uint32_t* err, Tout* total, int32_t* maxv,
-                                                            uint32_t spin_limit = SPIN_LIMIT) {
+                                                            uint32_t spin_limit = SPIN_LIMIT,
+                                                            int64_t prefetch_tiles = 0) {
   __shared__ Tout s_buf[SCAN_TILE + SCAN_TILE / 32];
   __shared__ Tout s_wsum[SCAN_THREADS / 32];
   __shared__ uint32_t s_tile;
@@ -38,6 +40,15 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan_excl(const Tin* __restric
   __syncthreads();
   const int64_t tile = s_tile;
   const int64_t tbase = tile * SCAN_TILE;
+  if (prefetch_tiles > 0 && tid == 0) {
+    // a whole tile, in bounds; the input is 16-byte aligned and a tile is
+    // 16 or 32 KB
+    const int64_t pbase = tbase + prefetch_tiles * SCAN_TILE;
+    if (pbase + SCAN_TILE <= n)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(in + pbase),
+                   "r"((uint32_t)(SCAN_TILE * sizeof(Tin)))
+                   : "memory");
+  }
   int32_t local_max = INT32_MIN;
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) {
@@ -80,19 +91,21 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan_excl(const Tin* __restric
     if (w < warp) wpre += s_wsum[w];
     tile_total += s_wsum[w];
   }
-  if (tid == 0) {
+  if (warp == 0) {
     uint64_t* st = status + tile;
     Tout excl = 0;
     if (tile == 0) {
-      st_relaxed(st, lb_pack(1, LB_INC, (uint64_t)tile_total));
+      if (lane == 0) st_relaxed(st, lb_pack(1, LB_INC, (uint64_t)tile_total));
     } else {
-      st_relaxed(st, lb_pack(1, LB_AGG, (uint64_t)tile_total));
-      excl = (Tout)lookback(status, tile, 1, 1, err, spin_limit);
-      st_relaxed(st, lb_pack(1, LB_INC, (uint64_t)(excl + tile_total)));
+      if (lane == 0) st_relaxed(st, lb_pack(1, LB_AGG, (uint64_t)tile_total));
+      excl = (Tout)lookback_warp(status, tile, 1, err, lane, spin_limit);
+      if (lane == 0) st_relaxed(st, lb_pack(1, LB_INC, (uint64_t)(excl + tile_total)));
     }
-    s_excl = excl;
-    if (CHECK && (uint64_t)(excl + tile_total) > LB_VALUE_MASK) atomicOr(err, DERR_OVERFLOW);
-    if (total && tbase + SCAN_TILE >= n) *total = excl + tile_total;
+    if (lane == 0) {
+      s_excl = excl;
+      if (CHECK && (uint64_t)(excl + tile_total) > LB_VALUE_MASK) atomicOr(err, DERR_OVERFLOW);
+      if (total && tbase + SCAN_TILE >= n) *total = excl + tile_total;
+    }
   }
   __syncthreads();
   Tout run = s_excl + wpre + incl - sum;
@@ -122,8 +135,11 @@ wedge_status run_scan(const Tin* in, Tout* out, int64_t n, Tout* total, int32_t*
   uint32_t* ctr = static_cast<uint32_t*>(scratch);
   uint64_t* status = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + 256);
   WEDGE_CUDA_TRY(cudaMemsetAsync(scratch, 0, 256 + (size_t)tiles * sizeof(uint64_t), s), name);
+  // L2 prefetch about one wave of CTAs ahead (six 34 KB tile buffers fit an SM)
+  const int64_t prefetch = (reinterpret_cast<uintptr_t>(in) & 15) == 0 ? 6 * (int64_t)sm_count() : 0;
   return launch(name, s, [&] {
-    k_scan_excl<Tin, Tout><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, status, ctr, derr, total, maxv);
+    k_scan_excl<Tin, Tout><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, status, ctr, derr, total, maxv,
+                                                                    SPIN_LIMIT, prefetch);
   });
 }
 
