@@ -7,9 +7,12 @@
 // sample indices; persistent CTAs (one wave: SMs x resident CTAs) pop tiles
 // from an atomic ticket until the list is exhausted, so small and large
 // requests share the GPU without per-request launches, synchronisations or
-// tail effects. A tile is drawn either one sample per thread or one sample
-// per warp (33-way cooperative searches), as the launch configuration says
-// for the tile's class. Samples are keyed by (seed, bin, tag, index) exactly
+// tail effects. The tile list is implicit: the streams are stored in
+// hand-out order with their first tile, so building a batch costs one entry
+// per stream, not per tile. A tile is drawn either per thread, two samples
+// in lockstep so that two chains of dependent loads are in flight, or one
+// sample per warp (33-way cooperative searches), as the launch
+// configuration says for the stream's class. Samples are keyed by (seed, bin, tag, index) exactly
 // as in wedge_sample, so every request's counts are bit-identical to a plain
 // wedge_sample call with the same parameters, whatever the mix and mapping.
 #include <string.h>
@@ -38,34 +41,34 @@ struct BatchGraph {
   wedge_record* records;  // global-stream records or nullptr
 };
 
+// A stream's tiles are samples_per_tile consecutive samples each (the last
+// one shorter); the streams are stored in the order their tiles are handed
+// out, and tile_begin is the stream's first tile in that order, so a ticket
+// finds its stream by binary search and no per-tile list is built.
 struct BatchStream {
   int64_t start, len;
   uint64_t p, wbase, k;
-  uint64_t first;  // first sample index
+  uint64_t first;       // first sample index
+  uint64_t tile_begin;  // first tile of this stream
   uint32_t bin, tag;
   uint32_t req;
-  uint32_t pad;
-};
-
-struct BatchTile {
-  uint64_t first;     // first sample index
-  uint32_t stream;
-  uint32_t count;     // samples in the tile
-  uint32_t mapping;   // WEDGE_MAP_THREAD or WEDGE_MAP_WARP
-  uint32_t pad;
+  uint32_t mapping;     // WEDGE_MAP_THREAD or WEDGE_MAP_WARP
 };
 
 constexpr int STAT_N = WEDGE_STAT_BINS * WEDGE_STAT_BINS;
 
 template <int THREADS>
-__global__ __launch_bounds__(THREADS) void k_sample_batch(const BatchGraph* __restrict__ graphs,
-                                                          const BatchStream* __restrict__ streams,
-                                                          const BatchTile* __restrict__ tiles, uint32_t n_tiles,
-                                                          uint32_t* ticket, unsigned long long* counters,
-                                                          unsigned long long* stats) {
+__global__ __launch_bounds__(THREADS, 1024 / THREADS) void k_sample_batch(const BatchGraph* __restrict__ graphs,
+                                                                          const BatchStream* __restrict__ streams,
+                                                                          uint32_t n_streams, uint32_t n_tiles,
+                                                                          uint32_t samples_per_tile, uint32_t* ticket,
+                                                                          unsigned long long* counters,
+                                                                          unsigned long long* stats) {
   constexpr int WARPS = THREADS / 32;
   __shared__ uint32_t s_t;
-  __shared__ BatchTile s_tile;
+  __shared__ uint32_t s_stream;
+  __shared__ uint64_t s_first;
+  __shared__ uint32_t s_count;
   __shared__ BatchStream s_st;
   __shared__ BatchGraph s_g;
   __shared__ uint64_t s_lo[WEDGE_MAX_BINS];
@@ -80,12 +83,21 @@ __global__ __launch_bounds__(THREADS) void k_sample_batch(const BatchGraph* __re
     const uint32_t t = s_t;
     if (t >= n_tiles) break;
     if (tid == 0) {
-      s_tile = tiles[t];
-      s_st = streams[s_tile.stream];
+      uint32_t lo = 0, hi = n_streams;  // the last stream whose first tile is <= t
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (streams[mid].tile_begin <= (uint64_t)t) lo = mid; else hi = mid;
+      }
+      s_stream = lo;
+      s_st = streams[lo];
+      s_first = ((uint64_t)t - s_st.tile_begin) * samples_per_tile;
+      s_count = (uint32_t)min((uint64_t)samples_per_tile, s_st.k - s_first);
       s_g = graphs[s_st.req];
     }
     __syncthreads();
-    const BatchTile tile = s_tile;
+    const uint32_t stream = s_stream;
+    const uint64_t tile_first = s_first;
+    const uint32_t tile_count = s_count;
     const BatchStream st = s_st;
     const BatchGraph g = s_g;
     const bool global = st.tag != 0;
@@ -95,16 +107,10 @@ __global__ __launch_bounds__(THREADS) void k_sample_batch(const BatchGraph* __re
     __syncthreads();
     const BinTable bt{s_lo, g.nb, g.pow2};
     uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
-    const bool per_warp = tile.mapping == WEDGE_MAP_WARP;
+    const bool per_warp = st.mapping == WEDGE_MAP_WARP;
     const int step = per_warp ? WARPS : THREADS;
     const int me = per_warp ? warp : tid;
-    for (int j = me; j < (int)tile.count; j += step) {
-      const uint64_t local = tile.first + (uint64_t)j;
-      const uint64_t s = st.first + local;  // sample index in the stream
-      const Philox4 r = philox4x32_10((uint32_t)s, (uint32_t)(s >> 32), st.bin, st.tag, g.seed_lo, g.seed_hi);
-      const Wedge w = per_warp ? draw_wedge_warp(g.g, st.start, st.len, st.p, st.wbase, r, lane)
-                               : draw_wedge_thread(g.g, st.start, st.len, st.p, st.wbase, r);
-      if (per_warp && lane != 0) continue;  // lane 0 records the warp's sample
+    auto record = [&](const Wedge& w, uint64_t local) {
       if (!global) {
         if (!w.closed) {
           q0 += 1;
@@ -134,6 +140,29 @@ __global__ __launch_bounds__(THREADS) void k_sample_batch(const BatchGraph* __re
           g.records[local] = rec;
         }
       }
+    };
+    if (per_warp) {
+      for (int j = me; j < (int)tile_count; j += step) {
+        const uint64_t local = tile_first + (uint64_t)j;
+        const uint64_t s = st.first + local;  // sample index in the stream
+        const Philox4 r = philox4x32_10((uint32_t)s, (uint32_t)(s >> 32), st.bin, st.tag, g.seed_lo, g.seed_hi);
+        const Wedge w = draw_wedge_warp(g.g, st.start, st.len, st.p, st.wbase, r, lane);
+        if (lane == 0) record(w, local);  // lane 0 records the warp's sample
+      }
+    } else {
+      // two samples per thread in lockstep (j and j + step), so two chains of
+      // dependent loads are in flight; an odd last one draws a copy of itself
+      for (int j = me; j < (int)tile_count; j += 2 * step) {
+        const bool two = j + step < (int)tile_count;
+        const uint64_t la = tile_first + (uint64_t)j, lb = two ? la + (uint64_t)step : la;
+        const uint64_t sa = st.first + la, sb = st.first + lb;
+        const Philox4 ra = philox4x32_10((uint32_t)sa, (uint32_t)(sa >> 32), st.bin, st.tag, g.seed_lo, g.seed_hi);
+        const Philox4 rb = philox4x32_10((uint32_t)sb, (uint32_t)(sb >> 32), st.bin, st.tag, g.seed_lo, g.seed_hi);
+        Wedge wa, wb;
+        draw_wedge_thread2(g.g, st.start, st.len, st.p, st.wbase, ra, rb, wa, wb);
+        record(wa, la);
+        if (two) record(wb, lb);
+      }
     }
     {
       const uint32_t w0 = __reduce_add_sync(FULL_MASK, q0), w1 = __reduce_add_sync(FULL_MASK, q1);
@@ -149,7 +178,7 @@ __global__ __launch_bounds__(THREADS) void k_sample_batch(const BatchGraph* __re
     if (tid < 4) {
       uint32_t tot = 0;
       for (int w = 0; w < WARPS; ++w) tot += s_q[w][tid];
-      if (tot) atomicAdd(counters + (size_t)tile.stream * 4 + tid, (unsigned long long)tot);
+      if (tot) atomicAdd(counters + (size_t)stream * 4 + tid, (unsigned long long)tot);
     }
     if (global) {
       for (int i = tid; i < STAT_N; i += THREADS)
@@ -191,6 +220,7 @@ struct wedge_batch {
   int n_reqs;
   uint32_t block_threads;
   uint32_t n_tiles;
+  uint32_t samples_per_tile;
   uint32_t grid;
   // host copies
   std::vector<wedge_counts> base;      // per request: n_bins, n_b, p_b, p_total (counts filled from results)
@@ -199,7 +229,6 @@ struct wedge_batch {
   // device
   BatchGraph* d_graphs = nullptr;
   BatchStream* d_streams = nullptr;
-  BatchTile* d_tiles = nullptr;
   unsigned char* d_out = nullptr;      // [ticket 256 B][counters n_streams*4][stats n_reqs*STAT_N]
   size_t out_bytes = 0;
   // pinned host result
@@ -219,7 +248,6 @@ void batch_release(wedge_batch* b) {
   if (b->h_out) pinned_free(b->h_out, b->out_bytes);
   dfree(b->d_graphs, nullptr);
   dfree(b->d_streams, nullptr);
-  dfree(b->d_tiles, nullptr);
   dfree(b->d_out, nullptr);
   delete b;
 }
@@ -233,16 +261,16 @@ wedge_status enqueue_batch(wedge_batch* b, cudaStream_t s) {
   // graph launch is what wedge_batch_launch counts and times).
   switch (b->block_threads) {
     case 128:
-      k_sample_batch<128><<<b->grid, 128, 0, s>>>(b->d_graphs, b->d_streams, b->d_tiles, b->n_tiles, ticket, counters,
-                                                  stats);
+      k_sample_batch<128><<<b->grid, 128, 0, s>>>(b->d_graphs, b->d_streams, (uint32_t)b->streams.size(),
+                                                  b->n_tiles, b->samples_per_tile, ticket, counters, stats);
       break;
     case 512:
-      k_sample_batch<512><<<b->grid, 512, 0, s>>>(b->d_graphs, b->d_streams, b->d_tiles, b->n_tiles, ticket, counters,
-                                                  stats);
+      k_sample_batch<512><<<b->grid, 512, 0, s>>>(b->d_graphs, b->d_streams, (uint32_t)b->streams.size(),
+                                                  b->n_tiles, b->samples_per_tile, ticket, counters, stats);
       break;
     default:
-      k_sample_batch<256><<<b->grid, 256, 0, s>>>(b->d_graphs, b->d_streams, b->d_tiles, b->n_tiles, ticket, counters,
-                                                  stats);
+      k_sample_batch<256><<<b->grid, 256, 0, s>>>(b->d_graphs, b->d_streams, (uint32_t)b->streams.size(),
+                                                  b->n_tiles, b->samples_per_tile, ticket, counters, stats);
       break;
   }
   WEDGE_CUDA_TRY(cudaGetLastError(), "wedge_batch: launch");
@@ -275,7 +303,6 @@ extern "C" wedge_status wedge_batch_create(const wedge_request* reqs, int n_reqs
   b->block_threads = c.block_threads;
   b->base.resize((size_t)n_reqs);
   std::vector<BatchGraph> graphs((size_t)n_reqs);
-  std::vector<BatchTile> tiles;
   auto bail = [&](wedge_status e) {
     batch_release(b);
     return e;
@@ -329,20 +356,10 @@ extern "C" wedge_status wedge_batch_create(const wedge_request* reqs, int n_reqs
       st.bin = bin;
       st.tag = tag;
       st.req = (uint32_t)r;
-      st.pad = 0;
-      const uint32_t sidx = (uint32_t)b->streams.size();
+      st.mapping = class_mapping(c, stream_class(len));
+      st.tile_begin = 0;
       b->streams.push_back(st);
       b->stream_bin.push_back(tag == 0 ? (int)bin : -1);
-      const uint32_t map = class_mapping(c, stream_class(len));
-      for (uint64_t f = 0; f < k; f += c.samples_per_tile) {
-        BatchTile t;
-        t.first = f;
-        t.stream = sidx;
-        t.count = (uint32_t)std::min<uint64_t>(c.samples_per_tile, k - f);
-        t.mapping = map;
-        t.pad = 0;
-        tiles.push_back(t);
-      }
     };
     uint64_t wacc = 0;
     for (uint32_t k = 2; k < inf.n_bins; ++k) {
@@ -352,13 +369,31 @@ extern "C" wedge_status wedge_batch_create(const wedge_request* reqs, int n_reqs
     }
     add(0, inf.n_wedge_vertices, inf.p_total, k_glob, 0u, 1u, 0ULL);
   }
-  if (tiles.size() > (size_t)UINT32_MAX / 2) return bail(fail(WEDGE_EINVAL, "wedge_batch_create: too many tiles"));
-  // Longest-first order: warp-mapped tiles and the largest streams start first.
-  std::stable_sort(tiles.begin(), tiles.end(), [&](const BatchTile& x, const BatchTile& y) {
-    if (x.mapping != y.mapping) return x.mapping == WEDGE_MAP_WARP;
-    return b->streams[x.stream].len > b->streams[y.stream].len;
-  });
-  b->n_tiles = (uint32_t)tiles.size();
+  // Longest-first order: warp-mapped streams and the largest streams hand out
+  // their tiles first; each stream's first tile follows from the tile counts.
+  {
+    std::vector<uint32_t> order(b->streams.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (uint32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+      const BatchStream &sx = b->streams[x], &sy = b->streams[y];
+      if (sx.mapping != sy.mapping) return sx.mapping == WEDGE_MAP_WARP;
+      return sx.len > sy.len;
+    });
+    std::vector<BatchStream> streams(order.size());
+    std::vector<int> bins(order.size());
+    uint64_t next_tile = 0;
+    for (size_t i = 0; i < order.size(); ++i) {
+      streams[i] = b->streams[order[i]];
+      bins[i] = b->stream_bin[order[i]];
+      streams[i].tile_begin = next_tile;
+      next_tile += (streams[i].k + c.samples_per_tile - 1) / c.samples_per_tile;
+    }
+    if (next_tile > (uint64_t)UINT32_MAX / 2) return bail(fail(WEDGE_EINVAL, "wedge_batch_create: too many tiles"));
+    b->streams.swap(streams);
+    b->stream_bin.swap(bins);
+    b->n_tiles = (uint32_t)next_tile;
+    b->samples_per_tile = c.samples_per_tile;
+  }
   switch (b->block_threads) {
     case 128: b->grid = (uint32_t)resident_blocks<128>(); break;
     case 512: b->grid = (uint32_t)resident_blocks<512>(); break;
@@ -370,8 +405,6 @@ extern "C" wedge_status wedge_batch_create(const wedge_request* reqs, int n_reqs
   b->out_bytes = 256 + (b->streams.size() * 4 + (size_t)n_reqs * STAT_N) * sizeof(unsigned long long);
   if ((st = dalloc_n(&b->d_graphs, std::max<size_t>(graphs.size(), 1), s, "wedge_batch_create")) != WEDGE_OK) return bail(st);
   if ((st = dalloc_n(&b->d_streams, std::max<size_t>(b->streams.size(), 1), s, "wedge_batch_create")) != WEDGE_OK)
-    return bail(st);
-  if ((st = dalloc_n(&b->d_tiles, std::max<size_t>(tiles.size(), 1), s, "wedge_batch_create")) != WEDGE_OK)
     return bail(st);
   if ((st = dalloc(reinterpret_cast<void**>(&b->d_out), b->out_bytes, s, "wedge_batch_create")) != WEDGE_OK)
     return bail(st);
@@ -385,10 +418,6 @@ extern "C" wedge_status wedge_batch_create(const wedge_request* reqs, int n_reqs
   if (!b->streams.empty()) {
     e = cudaMemcpyAsync(b->d_streams, b->streams.data(), b->streams.size() * sizeof(BatchStream),
                         cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "wedge_batch_create"));
-  }
-  if (!tiles.empty()) {
-    e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return bail(cuda_fail(e, "wedge_batch_create"));
   }
   e = cudaStreamSynchronize(s);

@@ -104,6 +104,101 @@ __device__ __forceinline__ Wedge draw_wedge_thread(const GraphView& g, int64_t s
   return w;
 }
 
+// Two wedges of one stream drawn in lockstep by one thread: the same results
+// as two draw_wedge_thread calls, with each step of the two searches issuing
+// both loads before using either, so two dependent chains of random loads
+// are in flight per thread instead of one. A search that has finished keeps
+// loading a valid index (its current lower bound) until the other ends.
+__device__ __forceinline__ void row_contains2(const int32_t* __restrict__ adj, int64_t la, int64_t ha, int32_t xa,
+                                              int64_t lb, int64_t hb, int32_t xb, bool& fa, bool& fb) {
+  while (ha - la > 8 || hb - lb > 8) {
+    const bool sa = ha - la > 8, sb = hb - lb > 8;
+    const int64_t ma = sa ? la + ((ha - la) >> 1) : la;
+    const int64_t mb = sb ? lb + ((hb - lb) >> 1) : lb;
+    const int32_t ya = __ldg(adj + ma), yb = __ldg(adj + mb);
+    if (sa) {
+      if (ya <= xa) la = ma; else ha = ma;
+    }
+    if (sb) {
+      if (yb <= xb) lb = mb; else hb = mb;
+    }
+  }
+  // at most 8 entries left in each: scan both in step
+  bool da = false, db = false;
+  fa = fb = false;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool ra = !da && la + i < ha, rb = !db && lb + i < hb;
+    const int32_t ya = ra ? __ldg(adj + la + i) : 0, yb = rb ? __ldg(adj + lb + i) : 0;
+    if (ra) {
+      if (ya == xa) fa = true;
+      if (ya >= xa) da = true;
+    }
+    if (rb) {
+      if (yb == xb) fb = true;
+      if (yb >= xb) db = true;
+    }
+  }
+}
+
+__device__ __forceinline__ void draw_wedge_thread2(const GraphView& g, int64_t start, int64_t len, uint64_t p,
+                                                   uint64_t wbase, const Philox4& ra, const Philox4& rb, Wedge& wa,
+                                                   Wedge& wb) {
+  const uint64_t Ta = wbase + mulhi64((uint64_t)ra.r0 | ((uint64_t)ra.r1 << 32), p);
+  const uint64_t Tb = wbase + mulhi64((uint64_t)rb.r0 | ((uint64_t)rb.r1 << 32), p);
+  int64_t la = start, ha = start + len, lb = start, hb = start + len;  // W[lo] <= T < W[hi]
+  while (ha - la > 1 || hb - lb > 1) {
+    const bool sa = ha - la > 1, sb = hb - lb > 1;
+    const int64_t ma = sa ? la + ((ha - la) >> 1) : la;
+    const int64_t mb = sb ? lb + ((hb - lb) >> 1) : lb;
+    const uint64_t xa = __ldg(g.W + ma), xb = __ldg(g.W + mb);
+    if (sa) {
+      if (xa <= Ta) la = ma; else ha = ma;
+    }
+    if (sb) {
+      if (xb <= Tb) lb = mb; else hb = mb;
+    }
+  }
+  wa.v0 = checked_ldg(g.L, la, g.n_L, g.err);
+  wb.v0 = checked_ldg(g.L, lb, g.n_L, g.err);
+  const int64_t oa = checked_ldg(g.off, wa.v0, g.n + 1, g.err);
+  const int64_t ob = checked_ldg(g.off, wb.v0, g.n + 1, g.err);
+  wa.d0 = checked_ldg(g.off, (int64_t)wa.v0 + 1, g.n + 1, g.err) - oa;
+  wb.d0 = checked_ldg(g.off, (int64_t)wb.v0 + 1, g.n + 1, g.err) - ob;
+  const uint64_t dma = (uint64_t)(wa.d0 - 1), dmb = (uint64_t)(wb.d0 - 1);
+  const uint64_t ua = mulhi64((uint64_t)ra.r2 | ((uint64_t)ra.r3 << 32), (uint64_t)wa.d0 * dma);
+  const uint64_t ub = mulhi64((uint64_t)rb.r2 | ((uint64_t)rb.r3 << 32), (uint64_t)wb.d0 * dmb);
+  const uint64_t ia = ua / dma, ib = ub / dmb;
+  const uint64_t jpa = ua - ia * dma, jpb = ub - ib * dmb;
+  const uint64_t ja = jpa + (jpa >= ia ? 1ULL : 0ULL), jb = jpb + (jpb >= ib ? 1ULL : 0ULL);
+  wa.v1 = checked_ldg(g.adj, oa + (int64_t)ia, g.n_adj, g.err);
+  wa.v2 = checked_ldg(g.adj, oa + (int64_t)ja, g.n_adj, g.err);
+  wb.v1 = checked_ldg(g.adj, ob + (int64_t)ib, g.n_adj, g.err);
+  wb.v2 = checked_ldg(g.adj, ob + (int64_t)jb, g.n_adj, g.err);
+  const int64_t o1a = checked_ldg(g.off, wa.v1, g.n + 1, g.err);
+  const int64_t o2a = checked_ldg(g.off, wa.v2, g.n + 1, g.err);
+  const int64_t o1b = checked_ldg(g.off, wb.v1, g.n + 1, g.err);
+  const int64_t o2b = checked_ldg(g.off, wb.v2, g.n + 1, g.err);
+  wa.d1 = checked_ldg(g.off, (int64_t)wa.v1 + 1, g.n + 1, g.err) - o1a;
+  wa.d2 = checked_ldg(g.off, (int64_t)wa.v2 + 1, g.n + 1, g.err) - o2a;
+  wb.d1 = checked_ldg(g.off, (int64_t)wb.v1 + 1, g.n + 1, g.err) - o1b;
+  wb.d2 = checked_ldg(g.off, (int64_t)wb.v2 + 1, g.n + 1, g.err) - o2b;
+  const bool oka = in_bounds((uint64_t)(o1a + wa.d1), (uint64_t)g.n_adj + 1, g.err) &&
+                   in_bounds((uint64_t)(o2a + wa.d2), (uint64_t)g.n_adj + 1, g.err);
+  const bool okb = in_bounds((uint64_t)(o1b + wb.d1), (uint64_t)g.n_adj + 1, g.err) &&
+                   in_bounds((uint64_t)(o2b + wb.d2), (uint64_t)g.n_adj + 1, g.err);
+  // closure: the larger-(degree, id) endpoint searched in the other's row
+  const bool a1 = wa.d1 < wa.d2 || (wa.d1 == wa.d2 && wa.v1 < wa.v2);
+  const bool b1 = wb.d1 < wb.d2 || (wb.d1 == wb.d2 && wb.v1 < wb.v2);
+  const int64_t rla = a1 ? o1a : o2a, rha = a1 ? o1a + wa.d1 : o2a + wa.d2;
+  const int64_t rlb = b1 ? o1b : o2b, rhb = b1 ? o1b + wb.d1 : o2b + wb.d2;
+  bool fa, fb;
+  row_contains2(g.adj, oka ? rla : 0, oka ? rha : 0, a1 ? wa.v2 : wa.v1, okb ? rlb : 0, okb ? rhb : 0,
+                b1 ? wb.v2 : wb.v1, fa, fb);
+  wa.closed = oka && fa;
+  wb.closed = okb && fb;
+}
+
 // ------------------------------------------------------------------ warp --
 
 // Largest j in [lo, hi) with W[j] <= T, given W[lo] <= T < W[hi]. Same
