@@ -473,13 +473,16 @@ def bench_serving(wedge, graphgen, torch, rates, n_requests, n_graphs=64, seed=5
         arrivals = np.cumsum(gaps)
         reqs = [(int(rng.integers(0, len(ids))), int(rng.integers(1, 1 << 40)), float(rng.choice(eps_set)),
                  bool(rng.random() < upload_frac)) for _ in range(n_requests)]
+        # the uploads' edge lists, generated before either timed loop: both
+        # paths upload the same graphs
+        up_edges = {j: gen_edges(1000 + j) for j in range(n_requests) if reqs[j][3]}
         # continuous-batching server
         srv.stats(reset=True)
         tickets = [None] * n_requests
         uploads = []
 
         def uploader(i):
-            s, d, n = gen_edges(1000 + i)
+            s, d, n = up_edges[i]
             try:
                 t0 = time.perf_counter()
                 srv.add_graph(s, d, n)
@@ -511,7 +514,6 @@ def bench_serving(wedge, graphgen, torch, rates, n_requests, n_graphs=64, seed=5
         # plain per-request path, same arrivals and uploads, one call at a time
         lat = []
         samples = 0
-        up_edges = [gen_edges(1000 + j) if reqs[j][3] else None for j in range(n_requests)]
         t_start = time.perf_counter()
         for j, (gi, sd, eps, is_upload) in enumerate(reqs):
             delay = t_start + arrivals[j] - time.perf_counter()
