@@ -285,12 +285,15 @@ WEDGE_API wedge_status wedge_sample(const wedge_graph* g, const wedge_bins* b, c
  * chosen per stream class by the number of vertices the stream searches
  * (small < 2^12, medium < 2^20, large). block_threads is 128, 256 or 512
  * (0 = 256); samples_per_tile defaults to 2048. wedge_autotune times
- * candidate configurations on the requests (budgets scaled down 8x) and
- * returns the fastest; results are cached per device and request-shape
- * signature in memory and, if the environment variable WEDGE_TUNE_CACHE
- * names a file, in that file.
+ * candidate configurations on the requests themselves (their own budgets
+ * when the samples total at most 1.5e9; above that, budgets and candidate
+ * tile sizes scaled down by the same factor, so each stream keeps its
+ * number of tiles) and returns the fastest; results are cached per device
+ * and request-shape signature in memory and, if the environment variable
+ * WEDGE_TUNE_CACHE names a file, in that file.
  *
- * wedge_batch_create builds the work list on the device (synchronising s)
+ * wedge_batch_create uploads one descriptor per stream (the tiles are
+ * implicit: each stream's first tile in hand-out order; synchronising s)
  * and captures clear + kernel + copy-back into a CUDA graph;
  * wedge_batch_launch replays it on s (reusable; asynchronous);
  * wedge_batch_results waits for the last launch and fills out[n_reqs].

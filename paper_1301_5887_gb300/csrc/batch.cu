@@ -603,30 +603,47 @@ extern "C" wedge_status wedge_autotune(const wedge_request* reqs, int n_reqs, we
       return WEDGE_OK;
     }
   }
-  // Probe requests: the same streams with budgets scaled down 8x (at least 64).
+  // Probe requests: the requests' own budgets when their samples total at most
+  // kProbeSamples, so each candidate is timed on the real work; above that,
+  // budgets and candidate tile sizes are both scaled down by the same factor
+  // f (budgets at least 64), so every stream keeps its number of tiles.
+  constexpr uint64_t kProbeSamples = 1500000000ULL;
   std::vector<wedge_request> probe(reqs, reqs + n_reqs);
   std::vector<std::vector<uint64_t>> kb((size_t)n_reqs);
+  std::vector<uint64_t> kgl((size_t)n_reqs, 0);
+  uint64_t total = 0;
   for (int r = 0; r < n_reqs; ++r) {
     const wedge_bins_info& inf = reqs[r].bins->info;
     kb[(size_t)r].assign(inf.n_bins, 0);
     uint64_t dflt = reqs[r].params.k_per_bin;
     if (!reqs[r].params.k_bin && dflt == 0) dflt = wedge_hoeffding_k(reqs[r].params.eps, reqs[r].params.delta);
+    const bool bins = !(reqs[r].params.flags & WEDGE_FLAG_NO_BINS);
     for (uint32_t k = 0; k < inf.n_bins; ++k) {
-      const uint64_t v = reqs[r].params.k_bin ? reqs[r].params.k_bin[k] : dflt;
-      kb[(size_t)r][k] = v ? std::max<uint64_t>(v / 8, 64) : 0;
+      kb[(size_t)r][k] = bins ? (reqs[r].params.k_bin ? reqs[r].params.k_bin[k] : dflt) : 0;
+      if (k >= 2 && inf.p_b[k] > 0) total += kb[(size_t)r][k];
     }
-    probe[(size_t)r].params.k_bin = kb[(size_t)r].data();
     uint64_t kg = reqs[r].params.k_global;
     if (kg == 0 && !(reqs[r].params.flags & WEDGE_FLAG_NO_GLOBAL))
       kg = wedge_hoeffding_k(reqs[r].params.eps, reqs[r].params.delta);
-    probe[(size_t)r].params.k_global = kg ? std::max<uint64_t>(kg / 8, 64) : 0;
+    if (reqs[r].params.flags & WEDGE_FLAG_NO_GLOBAL) kg = 0;
+    kgl[(size_t)r] = kg;
+    if (inf.p_total > 0) total += kg;
+  }
+  const uint64_t f = std::max<uint64_t>(1, (total + kProbeSamples - 1) / kProbeSamples);
+  for (int r = 0; r < n_reqs; ++r) {
+    for (uint64_t& v : kb[(size_t)r]) v = v ? std::max<uint64_t>(v / f, 64) : 0;
+    probe[(size_t)r].params.k_bin = kb[(size_t)r].data();
+    const uint64_t kg = kgl[(size_t)r];
+    probe[(size_t)r].params.k_global = kg ? std::max<uint64_t>(kg / f, 64) : 0;
     if (kg == 0) probe[(size_t)r].params.flags |= WEDGE_FLAG_NO_GLOBAL;
     probe[(size_t)r].params.records = nullptr;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   WEDGE_CUDA_TRY(cudaEventCreate(&e0), "wedge_autotune");
   WEDGE_CUDA_TRY(cudaEventCreate(&e1), "wedge_autotune");
-  auto time_cfg = [&](const wedge_launch_config& c, float* ms) -> wedge_status {
+  auto time_cfg = [&](const wedge_launch_config& cfg, float* ms) -> wedge_status {
+    wedge_launch_config c = cfg;
+    c.samples_per_tile = std::max<uint32_t>(cfg.samples_per_tile / (uint32_t)std::min<uint64_t>(f, 1u << 20), 64u);
     wedge_batch* b = nullptr;
     wedge_status st = wedge_batch_create(probe.data(), n_reqs, &c, stream, &b);
     if (st != WEDGE_OK) return st;
@@ -661,7 +678,7 @@ extern "C" wedge_status wedge_autotune(const wedge_request* reqs, int n_reqs, we
       c.block_threads = bt;
       c.samples_per_tile = ts;
       float ms = 0.f;
-      if ((st = time_cfg(c, &ms)) != WEDGE_OK) break;
+      if ((st = time_cfg(c, &ms)) != WEDGE_OK) break;  // (time_cfg times ts / f)
       if (ms < best_ms) {
         best_ms = ms;
         best = c;
