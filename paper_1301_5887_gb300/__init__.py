@@ -658,7 +658,7 @@ def _config(cfg):
 
 
 class Batch:
-    """A planned batch (work list on the device, CUDA-graph-captured launch)."""
+    """A planned batch (one descriptor per stream on the device, CUDA-graph-captured launch)."""
 
     def __init__(self, requests: Requests, cfg=None, stream=None):
         lib = load()

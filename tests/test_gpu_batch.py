@@ -113,6 +113,32 @@ def test_batch_order_and_replay(mix):
     batch.free()
 
 
+@pytest.mark.parametrize("spt", [512, 1000, 4096])
+def test_batch_tiles_are_per_stream(mix, spt):
+    """The tile list is implicit: one stream per nonempty bin with a budget
+    (and the global stream), each cut into ceil(k / samples_per_tile) tiles;
+    the counts stay exact for tile sizes that do not divide the budgets."""
+    batch = wedge.Batch(wedge.Requests(mix), cfg={"samples_per_tile": spt})
+    info = batch.info()
+    batch.launch()
+    got = batch.results()
+    batch.free()
+    streams = tiles = 0
+    for r in mix:
+        bi = r["bins"].info()
+        for k in range(2, bi.n_bins):
+            if bi.p_b[k] > 0 and int(r["k_bin"][k]) > 0:
+                streams += 1
+                tiles += -(-int(r["k_bin"][k]) // spt)
+        if bi.p_total > 0 and r["k_global"] > 0:
+            streams += 1
+            tiles += -(-int(r["k_global"]) // spt)
+    assert info["streams"] == streams and info["tiles"] == tiles
+    ref = wedge.sample_batch(wedge.Requests(mix))
+    for a, b in zip(got, ref):
+        assert np.array_equal(a.counts_matrix(), b.counts_matrix()) and a.closed_global == b.closed_global
+
+
 def test_batch_records_match_plain(mix):
     r = mix[3]
     rec_b = torch.zeros((r["k_global"], 8), dtype=torch.int32, device="cuda")
