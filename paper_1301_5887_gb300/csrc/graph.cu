@@ -45,8 +45,27 @@ constexpr int DEDUP_THREADS = 384;
 constexpr int DEDUP_ITEMS = 16;
 constexpr int DEDUP_TILE = DEDUP_THREADS * DEDUP_ITEMS;
 
-__device__ __forceinline__ void count_digits(uint32_t* sh, uint64_t key, int passes) {
-  for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + (uint32_t)((key >> (8 * p)) & 255u)], 1u);
+// Edge histograms are kept as HIST_COPIES interleaved copies (bin d of copy c
+// at word d * HIST_COPIES + c, the copy chosen by lane), so the lanes of a
+// warp that add to random bins spread over more banks: the shared-memory
+// atomics of one warp instruction conflict far less often.
+constexpr int HIST_COPIES = 8;
+
+// NP > 0: the number of digits is a compile-time constant, so the loop
+// unrolls and each digit is one byte permute of a half of the key.
+template <int NP>
+__device__ __forceinline__ void count_digits(uint32_t* sh, uint64_t key, int passes, uint32_t copy) {
+  uint32_t* shc = sh + copy;
+  if (NP > 0) {
+    const uint32_t lo = (uint32_t)key, hi = (uint32_t)(key >> 32);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const uint32_t d = __byte_perm(p < 4 ? lo : hi, 0u, 0x4440u | (uint32_t)(p & 3));
+      atomicAdd(&shc[(p * 256 + d) * HIST_COPIES], 1u);
+    }
+  } else {
+    for (int p = 0; p < passes; ++p) atomicAdd(&shc[(p * 256 + (uint32_t)((key >> (8 * p)) & 255u)) * HIST_COPIES], 1u);
+  }
 }
 
 // Expand edges to packed keys and accumulate the radix sort's digit
@@ -56,15 +75,19 @@ __device__ __forceinline__ void count_digits(uint32_t* sh, uint64_t key, int pas
 // VEC: src, dst and keys are 16-byte aligned, and each thread takes four
 // edges per step with 16-byte loads (the scalar form keeps too few bytes in
 // flight to stream at the HBM rate). WRITE false: histograms only (the sort's
-// first pass then computes the keys from the edges itself).
-template <bool VEC, bool WRITE>
-__global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+// first pass then computes the keys from the edges itself). NP > 0: passes
+// == NP, known at compile time.
+constexpr int EXPAND_THREADS = 512;
+
+template <bool VEC, bool WRITE, int NP = 0>
+__global__ __launch_bounds__(EXPAND_THREADS) void k_expand(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                                                 int64_t m, int32_t n, uint32_t b, uint64_t sentinel, int passes,
                                                 uint64_t* __restrict__ keys, unsigned long long* __restrict__ hist,
                                                 unsigned long long* __restrict__ hist_total, uint32_t* err) {
-  __shared__ uint32_t sh[SORT_MAX_PASSES * 256];
-  for (int i = threadIdx.x; i < SORT_MAX_PASSES * 256; i += blockDim.x) sh[i] = 0;
+  extern __shared__ uint32_t sh[];  // passes * 256 * HIST_COPIES words
+  for (int i = threadIdx.x; i < passes * 256 * HIST_COPIES; i += blockDim.x) sh[i] = 0;
   __syncthreads();
+  const uint32_t copy = threadIdx.x & (HIST_COPIES - 1);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t scalar_from = 0;
@@ -81,24 +104,46 @@ __global__ __launch_bounds__(256) void k_expand(const int32_t* __restrict__ src,
         __stcs(k2 + 2 * e, make_ulonglong2(k0, k1));
         __stcs(k2 + 2 * e + 1, make_ulonglong2(k2v, k3));
       }
-      count_digits(sh, k0, passes);
-      count_digits(sh, k1, passes);
-      count_digits(sh, k2v, passes);
-      count_digits(sh, k3, passes);
+      count_digits<NP>(sh, k0, passes, copy);
+      count_digits<NP>(sh, k1, passes, copy);
+      count_digits<NP>(sh, k2v, passes, copy);
+      count_digits<NP>(sh, k3, passes, copy);
     }
     scalar_from = m4 << 2;  // the last m mod 4 edges
   }
   for (int64_t e = scalar_from + t0; e < m; e += stride) {
     const uint64_t key = edge_key(__ldcs(src + e), __ldcs(dst + e), n, b, sentinel, err);
     if (WRITE) __stcs(keys + e, key);
-    count_digits(sh, key, passes);
+    count_digits<NP>(sh, key, passes, copy);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
-    if (sh[i]) {
-      atomicAdd(&hist[i], (unsigned long long)sh[i]);
-      atomicAdd(&hist_total[i], (unsigned long long)sh[i]);
+  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int c = 0; c < HIST_COPIES; ++c) v += sh[i * HIST_COPIES + c];
+    if (v) {
+      atomicAdd(&hist[i], (unsigned long long)v);
+      atomicAdd(&hist_total[i], (unsigned long long)v);
     }
+  }
+}
+
+// Launch of k_expand<VEC, WRITE, NP> with its histogram copies in dynamic
+// shared memory (above the 48 KB default: the attribute is set once).
+template <bool VEC, bool WRITE, int NP>
+wedge_status launch_expand(int grid, size_t smem, cudaStream_t s, const int32_t* src, const int32_t* dst, int64_t m,
+                           int32_t n, uint32_t b, uint64_t sentinel, int passes, uint64_t* keys,
+                           unsigned long long* hist, unsigned long long* hist_total, uint32_t* err) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    const cudaError_t e = cudaFuncSetAttribute(k_expand<VEC, WRITE, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(SORT_MAX_PASSES * 256 * HIST_COPIES * sizeof(uint32_t)));
+    if (e != cudaSuccess) return cuda_fail(e, "wedge_graph_build: shared memory");
+    attr_set = true;
+  }
+  k_expand<VEC, WRITE, NP><<<grid, EXPAND_THREADS, smem, s>>>(src, dst, m, n, b, sentinel, passes, keys, hist,
+                                                              hist_total, err);
+  return WEDGE_OK;
 }
 
 // Digit histograms of the transposed sort (the tp low bytes of w, the larger
@@ -557,24 +602,36 @@ extern "C" wedge_status wedge_graph_build(const int32_t* src, const int32_t* dst
       uint64_t* k_out = bb.keys_a + e0;
       const bool vec = ((reinterpret_cast<uintptr_t>(s_in) | reinterpret_cast<uintptr_t>(d_in) |
                          reinterpret_cast<uintptr_t>(k_out)) & 15) == 0;
-      // twice the usual grid: more resident loads in flight
+      // a few resident waves of CTAs (three fit an SM with the 57 KB of
+      // histogram copies at seven passes)
       const int64_t units = vec ? (len + 3) / 4 : len;
-      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((units + 255) / 256, (int64_t)sm_count() * 16));
+      const int grid = (int)std::max<int64_t>(
+          1, std::min<int64_t>((units + EXPAND_THREADS - 1) / EXPAND_THREADS, (int64_t)sm_count() * 6));
       unsigned long long* hist = sort_hist_area(bb.scratch);
-      return launch(write ? "expand_edges" : "edge_histograms", s, [&] {
-        if (vec && write)
-          k_expand<true, true><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out, hist,
-                                                    bb.fhist, bb.derr);
-        else if (vec)
-          k_expand<true, false><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out, hist,
-                                                     bb.fhist, bb.derr);
-        else if (write)
-          k_expand<false, true><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out, hist,
-                                                     bb.fhist, bb.derr);
-        else
-          k_expand<false, false><<<grid, 256, 0, s>>>(s_in, d_in, len, n_vertices, b, sentinel, passes, k_out, hist,
-                                                      bb.fhist, bb.derr);
+      const size_t hsmem = (size_t)passes * 256 * HIST_COPIES * sizeof(uint32_t);
+      wedge_status lst = WEDGE_OK;
+      wedge_status st2 = launch(write ? "expand_edges" : "edge_histograms", s, [&] {
+#define WEDGE_EXPAND(V, W, NP)                                                                                  \
+  lst = launch_expand<V, W, NP>(grid, hsmem, s, s_in, d_in, len, n_vertices, b, sentinel, passes, k_out, hist, \
+                                bb.fhist, bb.derr)
+        if (vec && write) WEDGE_EXPAND(true, true, 0);
+        else if (write) WEDGE_EXPAND(false, true, 0);
+        else if (!vec) WEDGE_EXPAND(false, false, 0);
+        else {
+          switch (passes) {  // the fused path at scale: digits unrolled
+            case 1: WEDGE_EXPAND(true, false, 1); break;
+            case 2: WEDGE_EXPAND(true, false, 2); break;
+            case 3: WEDGE_EXPAND(true, false, 3); break;
+            case 4: WEDGE_EXPAND(true, false, 4); break;
+            case 5: WEDGE_EXPAND(true, false, 5); break;
+            case 6: WEDGE_EXPAND(true, false, 6); break;
+            case 7: WEDGE_EXPAND(true, false, 7); break;
+            default: WEDGE_EXPAND(true, false, 8); break;
+          }
+        }
+#undef WEDGE_EXPAND
       });
+      return st2 != WEDGE_OK ? st2 : lst;
     };
     // sort of `len` edges from s_in/d_in into keys_a/keys_b at e0
     auto expand_sort = [&](const int32_t* s_in, const int32_t* d_in, int64_t e0, int64_t len, uint64_t** out) {
