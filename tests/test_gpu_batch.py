@@ -179,3 +179,23 @@ def test_batch_edge_cases(mix):
     assert e.value.status == 1
     with pytest.raises(wedge.WedgeError):
         wedge.sample_batch(wedge.Requests(mix[:1]), cfg={"block_threads": 100})
+
+
+def test_autotune_scaled_probe_for_large_batches(mix):
+    """Requests totalling more than 1.5e9 samples are tuned on budgets and
+    tile sizes scaled down by the same factor; the chosen shape is one of the
+    candidates at full scale and the batch still equals plain calls."""
+    big = []
+    for r in mix:
+        item = dict(r)
+        item["k_bin"] = np.zeros_like(r["k_bin"])
+        item["k_global"] = 200_000_000
+        big.append(item)
+    cfg = wedge.autotune(wedge.Requests(big))
+    d = cfg.as_dict()
+    assert d["block_threads"] in (128, 256, 512) and d["samples_per_tile"] in (1024, 2048, 4096)
+    got = wedge.sample_batch(wedge.Requests(big), cfg=cfg)
+    for r, c in zip(big, got):
+        p = wedge.sample(r["graph"], r["bins"], seed=r["seed"], k_global=r["k_global"], k_bin=r["k_bin"])
+        assert c.k_global == p.k_global == r["k_global"] and c.closed_global == p.closed_global
+        assert np.array_equal(c.stats, p.stats)
